@@ -34,9 +34,12 @@
  *   bucket of pos at level L in the subproblem starting at o:
  *     ctr = (q_lo, q_hi, L | 1<<8, o_lo), q = pos >> 2, word = pos & 3,
  *     b = (word * k) >> 32           (k a power of two: the top log2(k) bits)
- *   Fisher-Yates partner for step i (position p = o+i), attempt a = 0,1,..:
- *     ctr = (p_lo, p_hi, L | 2<<8 | a<<16, o_lo); words 0..3 are tried in
- *     order with Lemire's bounded rejection for s = i+1 (Sec. 2.3, [0,s)).
+ *   Fisher-Yates partner for step i (position p = o+i), Lemire's bounded
+ *   rejection for s = i+1 (Sec. 2.3, read as [0,s)):
+ *     first word: ctr = (q_lo, q_hi, L | 2<<8, o_lo), q = p >> 2, word p & 3
+ *       (four consecutive positions share one Philox call, as bucket draws do);
+ *     on rejection, attempts a = 1,2,..: ctr = (p_lo, p_hi, L | 3<<8 | a<<16,
+ *       o_lo), words 0..3 tried in order.
  *
  * Parameters per level L: (k, T, B) = level[min(L, num_levels-1)].
  * max_levels = 0 means "no cap"; the recursion is then capped at 64 levels
@@ -113,6 +116,7 @@ int oracle_lemire_try(uint32_t bits, uint64_t s, uint32_t x, uint32_t *value)
 
 #define TAG_SCATTER 1u
 #define TAG_FY 2u
+#define TAG_FY_RETRY 3u
 
 uint32_t oracle_bucket(uint64_t seed, uint32_t level, uint64_t o, uint64_t pos, uint32_t k)
 {
@@ -128,16 +132,18 @@ uint64_t oracle_fy_draw(uint64_t seed, uint32_t level, uint64_t o, uint64_t i)
 {
     uint64_t p = o + i;
     uint64_t s = i + 1;
-    for (uint32_t attempt = 0; attempt < 65536u; ++attempt) {
-        uint32_t out[4];
+    uint64_t q = p >> 2;
+    uint32_t out[4];
+    uint32_t v;
+    philox_seeded(seed, (uint32_t)q, (uint32_t)(q >> 32), level | (TAG_FY << 8), (uint32_t)o, out);
+    if (oracle_lemire_try(32, s, out[p & 3], &v)) return v;
+    for (uint32_t attempt = 1; attempt < 65536u; ++attempt) {
         philox_seeded(seed, (uint32_t)p, (uint32_t)(p >> 32),
-                      level | (TAG_FY << 8) | (attempt << 16), (uint32_t)o, out);
-        for (int wd = 0; wd < 4; ++wd) {
-            uint32_t v;
+                      level | (TAG_FY_RETRY << 8) | (attempt << 16), (uint32_t)o, out);
+        for (int wd = 0; wd < 4; ++wd)
             if (oracle_lemire_try(32, s, out[wd], &v)) return v;
-        }
     }
-    return 0; /* unreachable in practice: 262144 consecutive rejections */
+    return 0; /* unreachable in practice: 262141 consecutive rejections */
 }
 
 /* ---------------------------------------------------------------- FY */

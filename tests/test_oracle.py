@@ -54,7 +54,8 @@ def test_philox_matches_triton():
 
 def test_bucket_and_fy_keying_match_triton():
     """bucket: counter (q_lo, q_hi, L|1<<8, o_lo), word pos&3, top log2 k bits;
-    FY: counter (p_lo, p_hi, L|2<<8|a<<16, o_lo), first accepted word."""
+    FY: first word from counter (q_lo, q_hi, L|2<<8, o_lo), word p&3; on
+    rejection counter (p_lo, p_hi, L|3<<8|a<<16, o_lo) for a = 1, 2, ..."""
     rng = np.random.default_rng(12)
     cases = []
     for _ in range(24):
@@ -68,23 +69,41 @@ def test_bucket_and_fy_keying_match_triton():
     for seed, level, o, pos, k in cases:
         q = pos >> 2
         rows.append([seed, q & 0xFFFFFFFF, q >> 32, level | (1 << 8), o & 0xFFFFFFFF])
-        rows.append([seed, pos & 0xFFFFFFFF, pos >> 32, level | (2 << 8), o & 0xFFFFFFFF])
+        rows.append([seed, q & 0xFFFFFFFF, q >> 32, level | (2 << 8), o & 0xFFFFFFFF])
+        rows.append([seed, pos & 0xFFFFFFFF, pos >> 32, level | (3 << 8) | (1 << 16), o & 0xFFFFFFFF])
     ref = _triton_philox(rows)
+
+    def lemire(x, s):  # Lemire 2019, Algorithm 5, in its own terms
+        prod = x * s
+        return prod >> 32 if (prod & 0xFFFFFFFF) >= (2**32 - s) % s else None
+
     for idx, (seed, level, o, pos, k) in enumerate(cases):
-        words = ref[2 * idx]
+        words = ref[3 * idx]
         want_b = words[pos & 3] >> (32 - int(math.log2(k)))
         assert oracle.bucket(seed, level, o, pos, k) == want_b
-        fy_words = ref[2 * idx + 1]
         i = pos - o
-        s = i + 1
-        want_j = None
-        for x in fy_words:  # Lemire 2019, Algorithm 5, in its own terms
-            prod = x * s
-            if (prod & 0xFFFFFFFF) >= (2**32 - s) % s:
-                want_j = prod >> 32
-                break
-        if want_j is not None:  # all four rejected: only for s close to 2^32
+        want_j = lemire(ref[3 * idx + 1][pos & 3], i + 1)
+        if want_j is None:
+            want_j = next((v for v in (lemire(x, i + 1) for x in ref[3 * idx + 2]) if v is not None), None)
+        if want_j is not None:
             assert oracle.fy_draw(seed, level, o, i) == want_j
+    # s = 2^31 + 1 rejects about half of all words, so the retry counters are used
+    i = 2**31
+    rows = []
+    for seed in range(1, 9):
+        rows.append([seed, (i >> 2) & 0xFFFFFFFF, i >> 34, 1 | (2 << 8), 0])
+        for a in range(1, 4):
+            rows.append([seed, i & 0xFFFFFFFF, i >> 32, 1 | (3 << 8) | (a << 16), 0])
+    ref = _triton_philox(rows)
+    retried = 0
+    for n, seed in enumerate(range(1, 9)):
+        words = [ref[4 * n][i & 3]] + [x for r in ref[4 * n + 1:4 * n + 4] for x in r]
+        vals = [lemire(x, i + 1) for x in words]
+        want = next((v for v in vals if v is not None), None)
+        retried += vals[0] is None
+        if want is not None:
+            assert oracle.fy_draw(seed, 1, 0, i) == want
+    assert retried > 0
 
 
 # ---------------------------------------------------------------- Lemire
