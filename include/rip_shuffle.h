@@ -1,0 +1,145 @@
+/*
+ * rip_shuffle.h -- C ABI of the GB300 in-place scatter-shuffle library.
+ *
+ * Problem (Sec. 1, Sec. 2.2 of Penschuck, "Engineering Shared-Memory Parallel
+ * Shuffling to Generate Random Permutations In-Place"): rearrange a sequence
+ * of n elements in place so that every permutation is equally likely, using
+ * only small auxiliary memory, reproducibly from a seed although the parallel
+ * schedule is not deterministic (Sec. 5).
+ *
+ * Method (Sec. 2.2 ScatterShuffle, Sec. 3.1-3.2 IpScShuf, Sec. 4 PIpScShuf):
+ * every element draws an independent uniform bucket among k; elements move
+ * into their bucket's contiguous region; every bucket is shuffled recursively;
+ * subproblems of at most `base` elements are finished by Fisher-Yates
+ * (Sec. 2.2, Fig. 1).  The result is a fixed ("canonical") function of
+ * (seed, n, plan): at each level, the elements of bucket b inside each tile of
+ * T elements keep their input order; the first B*floor(c/B) of them (c = their
+ * count) form "full blocks", the rest the "tail"; bucket b's region holds the
+ * full blocks of all tiles in tile order, then the tails in tile order.  The
+ * random draws come from Philox-4x32-10 keyed by the seed and counters built
+ * from (level, subproblem start, position); Fisher-Yates partners and bucket
+ * numbers use Lemire's bounded sampling (Sec. 2.3).  The exact keying is
+ * documented next to the device code and in the project's design notes.
+ *
+ * Conventions for every call below
+ *   - Pointers named `data`/`ptrs`/`ws` are DEVICE pointers on the current CUDA
+ *     device; the caller owns them and keeps them alive until the stream has
+ *     executed the work.  The library never frees caller memory.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All work is
+ *     enqueued asynchronously on it; host-side argument errors return before
+ *     anything is enqueued.
+ *   - elem_bytes is 4, 8 or 16; elements are opaque and only moved.
+ *     `data` must be aligned to elem_bytes.
+ *   - Return value: RIP_OK or a RIP_E* code below.  Errors detected on the
+ *     device (a wait limit that expired, workspace exhausted, an internal
+ *     consistency check) are recorded in a device status word; they are
+ *     reported by rip_get_device_status() and by the next call that syncs.
+ *   - n <= 1 is a no-op returning RIP_OK.
+ *   - Not thread-safe per device when the library-managed workspace is used
+ *     (ws == NULL): calls from several host threads must be serialised.
+ */
+#ifndef RIP_SHUFFLE_H
+#define RIP_SHUFFLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *rip_stream_t; /* same type as cudaStream_t */
+
+enum {
+    RIP_OK = 0,
+    RIP_EINVAL = 1,     /* invalid argument or plan                          */
+    RIP_ENOMEM = 2,     /* the library could not allocate its workspace      */
+    RIP_EWORKSPACE = 3, /* caller workspace too small / device pool exhausted */
+    RIP_ECUDA = 4,      /* a CUDA runtime call failed                         */
+    RIP_ETIMEOUT = 5,   /* a bounded device-side wait expired                 */
+    RIP_EINTERNAL = 6   /* a device-side consistency check failed            */
+};
+
+#define RIP_MAX_LEVEL_PARAMS 8
+
+/* Parameters of one scatter level (Sec. 3.1 "k buckets"; T and B define the
+ * canonical tile/block layout described above). */
+typedef struct {
+    uint32_t k;     /* buckets: power of two, 2 <= k <= 1024                   */
+    uint32_t block; /* B >= 1 elements per full block                           */
+    uint64_t tile;  /* T >= B, T % B == 0 (tiles start at each subproblem start) */
+} rip_level_params;
+
+/* A plan: level L uses level[min(L, num_levels - 1)].  A subproblem with
+ * m <= base elements, or one reaching level max_levels (0 = no cap, which the
+ * library treats as 64), is finished by Fisher-Yates (Sec. 3.2, "base case").
+ * base must be in [1, 2^32 - 1]. */
+typedef struct {
+    uint32_t num_levels;
+    uint32_t max_levels;
+    uint64_t base;
+    rip_level_params level[RIP_MAX_LEVEL_PARAMS];
+} rip_plan;
+
+/* Fills *plan with the library's default plan for n elements of elem_bytes:
+ * k = 256 (k = 64 below 128 MiB of data, the paper's rule in Sec. 5), base
+ * 4096, B sized so k*B*elem_bytes = 128 KiB, the root tile chosen so that the
+ * root has one tile per streaming multiprocessor and deeper levels one tile
+ * per subproblem.  Returns RIP_EINVAL for a NULL plan or bad elem_bytes. */
+int rip_default_plan(uint64_t n, uint32_t elem_bytes, rip_plan *plan);
+
+/* Bytes of device workspace rip_shuffle_ex needs for (n, elem_bytes, plan);
+ * plan NULL = default plan.  Returns 0 if the arguments are invalid. */
+size_t rip_shuffle_workspace_size(uint64_t n, uint32_t elem_bytes, const rip_plan *plan);
+
+/* Shuffle data[0..n) in place with the default plan and the library-managed
+ * workspace (allocated on first use per device, grown when a larger call
+ * needs it, kept until rip_release_workspace / process exit). */
+int rip_shuffle(void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed, rip_stream_t stream);
+
+/* Shuffle data[0..n) in place with an explicit plan (NULL = default).  If ws
+ * is non-NULL it must hold at least rip_shuffle_workspace_size() bytes and be
+ * 256-byte aligned; the call then allocates nothing.  If ws is NULL the
+ * library-managed workspace is used. */
+int rip_shuffle_ex(void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                   const rip_plan *plan, void *ws, size_t ws_bytes, rip_stream_t stream);
+
+/* Batched form (Sec. 6, many independent shuffles): array i (device pointer
+ * ptrs[i], ns[i] elements) is shuffled with seed base_seed + i, positions
+ * relative to its own start, all arrays with the same plan (NULL = default
+ * plan for the largest array).  ptrs and ns are HOST arrays of `count`
+ * entries; the arrays must not overlap.  ws as in rip_shuffle_ex. */
+size_t rip_shuffle_batched_workspace_size(const uint64_t *ns, uint32_t count, uint32_t elem_bytes,
+                                          const rip_plan *plan);
+int rip_shuffle_batched(void *const *ptrs, const uint64_t *ns, uint32_t count, uint32_t elem_bytes,
+                        uint64_t base_seed, const rip_plan *plan, void *ws, size_t ws_bytes,
+                        rip_stream_t stream);
+
+/* Position-dependent 64-bit digest of data[0..n), computed on the device:
+ *   H = sum_p splitmix64(p * 0x9E3779B97F4A7C15 ^ v(p)) mod 2^64,
+ * v(p) = splitmix64 chained over the element's 8-byte little-endian words.
+ * Used to compare outputs too large for a second host copy.  Synchronises
+ * `stream` and writes the digest to *out (host pointer). */
+int rip_digest(const void *data, uint64_t n, uint32_t elem_bytes, uint64_t *out, rip_stream_t stream);
+
+/* Synchronises `stream`, returns and clears the device status word of the
+ * current device (RIP_OK when no device-side error was recorded). */
+int rip_get_device_status(rip_stream_t stream);
+
+/* Frees the library-managed workspace of the current device. */
+int rip_release_workspace(void);
+
+/* Static message for a return code. */
+const char *rip_strerror(int code);
+
+/* Diagnostics of the last call on the current device, written to *out:
+ *   out[0] aux bytes the call's workspace layout uses,
+ *   out[1] number of scatter levels launched in place,
+ *   out[2] kernels launched by the call.
+ * Returns RIP_EINVAL if out is NULL. */
+int rip_last_call_info(uint64_t out[3]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RIP_SHUFFLE_H */

@@ -1,0 +1,543 @@
+// rip_api.cu -- host side of the C ABI: argument and plan validation, the
+// device workspace layout, and the level-synchronous driver of the recursion
+// (Sec. 3.2: scatter, then recurse into every bucket; Sec. 4: the buckets of a
+// level are independent, so one launch processes all of them).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "rip_internal.cuh"
+
+namespace rip {
+
+__device__ Status g_status;  // device status word of this library, per device
+
+namespace {
+
+constexpr uint32_t kMediumGrid = 16;
+constexpr size_t kClassifySmemBudget = 200 * 1024;
+
+struct LevelCaps {
+    uint32_t big = 0;       // subproblems that may run in place
+    uint64_t tiles = 0;
+    uint64_t pairs = 0;     // tiles x k
+    uint64_t children = 0;  // big x k
+    uint64_t pool = 0;      // elements
+    uint64_t dem = 0;
+};
+
+struct Layout {
+    size_t total = 0;
+    size_t arrays, lists_big0, lists_big1, small, medium, bigfy, counts, counters, pool_used;
+    size_t tiles, sp_tile_begin, C, FBc, TLc, tinfo, cand_prefix, child, words, pool, dem, mscratch;
+    uint32_t big_cap, small_cap, bigfy_cap, tile_cap, dem_cap, levels;
+    uint64_t pair_cap, child_cap, pool_cap, slot_count;
+    uint32_t small_max_m;
+    uint64_t aux_bytes;
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+uint32_t small_max_m_for(uint32_t w) {
+    const size_t fixed = small_fixed_smem();
+    const size_t m = (kSmemOptin - fixed) / (4 + w);
+    return (uint32_t)std::min<size_t>(m & ~size_t(7), kMediumMaxM);
+}
+
+DevPlan to_dev(const rip_plan& p) {
+    DevPlan d{};
+    d.num_levels = p.num_levels;
+    d.cap = p.max_levels ? p.max_levels : kDepthCap;
+    d.base = p.base;
+    for (uint32_t l = 0; l < p.num_levels; ++l) {
+        d.k[l] = p.level[l].k;
+        d.B[l] = p.level[l].block;
+        d.T[l] = p.level[l].tile;
+    }
+    return d;
+}
+
+bool pow2(uint32_t x) { return x && !(x & (x - 1)); }
+
+int validate_plan(const rip_plan& p, uint32_t w) {
+    if (p.num_levels < 1 || p.num_levels > RIP_MAX_LEVEL_PARAMS) return RIP_EINVAL;
+    if (p.base < 1 || p.base > 0xFFFFFFFFull) return RIP_EINVAL;
+    if (p.max_levels > kDepthCap) return RIP_EINVAL;
+    for (uint32_t l = 0; l < p.num_levels; ++l) {
+        const rip_level_params& q = p.level[l];
+        if (!pow2(q.k) || q.k < 2 || q.k > kMaxK) return RIP_EINVAL;
+        if (q.block < 1 || q.tile < q.block || q.tile % q.block) return RIP_EINVAL;
+        if (classify_smem_bytes(q.k, q.block, w) > kClassifySmemBudget) return RIP_EINVAL;
+        if (l > 0 && p.level[l - 1].block % q.block) return RIP_EINVAL;  // slot grids must nest
+    }
+    return RIP_OK;
+}
+
+bool valid_w(uint32_t w) { return w == 4 || w == 8 || w == 16; }
+
+// Expected-size model of the recursion used to size the workspace.  A level
+// can hold subproblems too large for one SM when mu_L + 10 sqrt(mu_L) + 64
+// reaches the smallest size that must run in place (mu_L = n / prod k; a
+// subproblem size is Binomial(n, 1/prod k), so larger deviations have
+// probability below e^-50 each).
+// Device-side capacity checks report RIP_EWORKSPACE if the model is exceeded.
+Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& p) {
+    Layout L{};
+    const DevPlan dp = to_dev(p);
+    L.small_max_m = small_max_m_for(w);
+    uint64_t nmax = 0, nsum = 0, slots = 0;
+    uint32_t bmin = 0xffffffffu;
+    for (uint32_t l = 0; l < p.num_levels; ++l) bmin = std::min(bmin, p.level[l].block);
+    for (uint64_t n : ns) {
+        nmax = std::max(nmax, n);
+        nsum += n;
+        slots += (n + bmin - 1) / bmin;
+    }
+    L.slot_count = slots;
+    const uint32_t narr = (uint32_t)ns.size();
+
+    std::vector<LevelCaps> caps;
+    uint64_t prodk = 1, max_children = 0;
+    uint64_t small_children = narr, bigfy_total = narr;
+    for (uint32_t lev = 0; lev < dp.cap && lev < 64; ++lev) {
+        const uint32_t li = dp.idx(lev);
+        const uint32_t k = p.level[li].k, B = p.level[li].block;
+        const uint64_t T = p.level[li].tile;
+        // smallest subproblem that runs in place at this level
+        uint64_t inplace_min = (uint64_t)kMediumMaxM + 1;
+        if (!small_solver_can_scatter(dp, kMediumMaxM, lev)) {  // eligibility is monotone in m
+            uint64_t lo = 1, hi = kMediumMaxM;                    // can(lo) or lo == 1, !can(hi)
+            while (hi - lo > 1) {
+                const uint64_t mid = (lo + hi) / 2;
+                if (small_solver_can_scatter(dp, mid, lev)) lo = mid; else hi = mid;
+            }
+            inplace_min = hi;
+        }
+        inplace_min = std::max<uint64_t>(inplace_min, dp.base + 1);
+        // per array: expected size at this level; count arrays for which big subproblems are possible
+        uint64_t big = 0, tiles = 0;
+        for (uint64_t n : ns) {
+            if (n < inplace_min) continue;
+            // a subproblem size at level L is Binomial(n, 1/prod k): mean mu, sd <= sqrt(mu)
+            const double mu = (double)n / (double)prodk;
+            if (mu + 10.0 * std::sqrt(mu) + 64.0 < (double)inplace_min) continue;
+            const uint64_t cnt = std::min<uint64_t>(prodk, n / inplace_min);
+            big += std::max<uint64_t>(cnt, 1);
+            tiles += n / T + std::max<uint64_t>(cnt, 1);
+        }
+        if (big == 0) break;
+        LevelCaps c;
+        c.big = (uint32_t)std::min<uint64_t>(big + 16, 0xffffffffull);
+        c.tiles = tiles + 16;
+        c.pairs = c.tiles * k;
+        c.children = (uint64_t)c.big * k;
+        // tails: (B-1)/2 per (tile, bucket) on average when counts are >> B, with a
+        // Hoeffding margin; otherwise every tile-bucket may be a tail
+        const double mu_tile = std::min<double>((double)T, (double)nmax / (double)prodk);
+        const double mu_c = mu_tile / k;
+        const double pairs = (double)c.pairs;
+        double tails;
+        if (mu_c >= 4.0 * B)
+            tails = pairs * (B - 1) / 2.0 * 1.05 + 20.0 * B * std::sqrt(pairs) + 4.0 * B * k;
+        else
+            tails = std::min<double>(pairs * (B - 1), (double)nsum + B);
+        // demoted blocks: at most one per (subproblem, bucket) plus two per subproblem.
+        // With counts >> B the tail total of a bucket is (close to) uniform mod B, so a
+        // bucket's last block is demoted with probability <= 1/2: Hoeffding margin.
+        const double dem_worst = std::min<double>((double)c.big * (k + 2), (double)nsum / B + c.big * 2.0);
+        const double pairs_sp = (double)c.big * k;
+        const double dem_blocks = mu_c >= 4.0 * B
+                                      ? std::min(dem_worst, pairs_sp / 2.0 + 20.0 * std::sqrt(pairs_sp) + 2.0 * c.big)
+                                      : dem_worst;
+        c.dem = (uint64_t)dem_worst + 16;
+        c.pool = (uint64_t)(tails + dem_blocks * B) + 64;
+        max_children = std::max<uint64_t>(max_children, (uint64_t)c.big * k);
+        caps.push_back(c);
+        small_children += (uint64_t)c.big * k;
+        bigfy_total += (uint64_t)c.big * k;
+        prodk = std::min<uint64_t>(prodk * k, (uint64_t)1 << 62);
+    }
+    L.levels = (uint32_t)caps.size();
+    for (const LevelCaps& c : caps) {
+        L.big_cap = std::max(L.big_cap, c.big);
+        L.tile_cap = (uint32_t)std::max<uint64_t>(L.tile_cap, c.tiles);
+        L.pair_cap = std::max(L.pair_cap, c.pairs);
+        L.child_cap = std::max(L.child_cap, c.children);
+        L.pool_cap = std::max(L.pool_cap, c.pool);
+        L.dem_cap = (uint32_t)std::max<uint64_t>(L.dem_cap, c.dem);
+    }
+    const uint64_t per_level_small = std::max<uint64_t>(narr, max_children);
+    L.small_cap = (uint32_t)std::min<uint64_t>(per_level_small + 16, 0x7fffffffull);
+    L.bigfy_cap = (uint32_t)std::min<uint64_t>(std::min<uint64_t>(bigfy_total, nsum / 2 + 16) + 16, 0x7fffffffull);
+    if (L.big_cap == 0) L.big_cap = 1;
+    if (L.tile_cap == 0) L.tile_cap = 1;
+
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + std::max<size_t>(bytes, 1), 256);
+        return o;
+    };
+    L.arrays = take(sizeof(ArrayDesc) * narr);
+    L.lists_big0 = take(sizeof(Sub) * L.big_cap);
+    L.lists_big1 = take(sizeof(Sub) * L.big_cap);
+    L.small = take(sizeof(Sub) * L.small_cap);
+    L.medium = take(sizeof(Sub) * L.small_cap);
+    L.bigfy = take(sizeof(Sub) * L.bigfy_cap);
+    L.counts = take(sizeof(uint32_t) * 8);
+    L.counters = take(sizeof(uint32_t) * 16);
+    L.pool_used = take(sizeof(uint64_t));
+    const size_t meta_start = off;
+    L.tiles = take(sizeof(TileRef) * L.tile_cap);
+    L.sp_tile_begin = take(sizeof(uint32_t) * L.big_cap);
+    L.C = take(sizeof(uint32_t) * L.pair_cap);
+    L.FBc = take(sizeof(uint32_t) * L.pair_cap);
+    L.TLc = take(sizeof(uint32_t) * L.pair_cap);
+    L.tinfo = take(sizeof(TileInfo) * L.tile_cap);
+    L.cand_prefix = take(sizeof(uint64_t) * (L.tile_cap + 1));
+    L.child = take(sizeof(ChildInfo) * L.child_cap);
+    L.words = take(L.levels ? sizeof(uint32_t) * L.slot_count : 0);
+    L.pool = take(L.levels ? (size_t)w * L.pool_cap : 0);
+    L.dem = take(sizeof(DemRec) * L.dem_cap);
+    L.mscratch = take((size_t)kMediumGrid * kMediumMaxM * w);
+    L.total = off;
+    (void)meta_start;
+    L.aux_bytes = off;
+    return L;
+}
+
+bool default_plan_impl(uint64_t n, uint32_t w, rip_plan* p, uint32_t num_sms) {
+    if (!valid_w(w) || !p) return false;
+    std::memset(p, 0, sizeof(*p));
+    const uint64_t bytes = n * w;
+    const uint32_t k = bytes < (128ull << 20) ? 64 : 256;  // Sec. 5: k = 64 below 128 MiB, else 256
+    uint32_t B = (uint32_t)((128u * 1024u) / (k * w));
+    B = std::max<uint32_t>(1, std::min<uint32_t>(B, 1024));
+    // level 0: one tile per SM (rounded to a multiple of B); deeper levels: one tile per subproblem
+    uint64_t T0 = (n + num_sms - 1) / std::max<uint32_t>(num_sms, 1);
+    T0 = std::max<uint64_t>(T0, (uint64_t)B * 64);
+    T0 = (T0 + B - 1) / B * B;
+    T0 = std::min<uint64_t>(T0, (uint64_t)B << 20);
+    T0 = T0 / B * B;
+    p->num_levels = 2;
+    p->level[0].k = k;
+    p->level[0].block = B;
+    p->level[0].tile = T0;
+    p->level[1].k = k;
+    p->level[1].block = B;
+    p->level[1].tile = std::min<uint64_t>((uint64_t)B << 20, (uint64_t)1 << 40) / B * B;
+    p->base = 4096;
+    p->max_levels = 0;
+    return true;
+}
+
+struct DevState {
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    uint32_t num_sms = 0;
+    Status* status = nullptr;
+    unsigned long long* digest_buf = nullptr;
+    uint64_t last_info[3] = {0, 0, 0};
+};
+
+std::mutex g_mutex;
+std::vector<DevState> g_dev;
+
+DevState* dev_state(int* dev_out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if ((int)g_dev.size() <= dev) g_dev.resize(dev + 1);
+    DevState& d = g_dev[dev];
+    if (!d.num_sms) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return nullptr;
+        d.num_sms = (uint32_t)sms;
+        void* sp = nullptr;
+        if (cudaGetSymbolAddress(&sp, g_status) != cudaSuccess) return nullptr;
+        d.status = reinterpret_cast<Status*>(sp);
+    }
+    if (dev_out) *dev_out = dev;
+    return &d;
+}
+
+int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns, uint32_t w, uint64_t base_seed,
+                const rip_plan* plan_in, void* ws, size_t ws_bytes, cudaStream_t stream) {
+    if (!valid_w(w)) return RIP_EINVAL;
+    for (size_t i = 0; i < ptrs.size(); ++i) {
+        if (ns[i] > 1 && !ptrs[i]) return RIP_EINVAL;
+        if (ns[i] > 1 && (reinterpret_cast<uintptr_t>(ptrs[i]) % w)) return RIP_EINVAL;
+        if (ns[i] > (1ull << 40)) return RIP_EINVAL;
+    }
+    int dev = 0;
+    DevState* ds = dev_state(&dev);
+    if (!ds) return RIP_ECUDA;
+    uint64_t nmax = 0;
+    for (uint64_t n : ns) nmax = std::max(nmax, n);
+    rip_plan plan;
+    if (plan_in) plan = *plan_in;
+    else default_plan_impl(nmax, w, &plan, ds->num_sms);
+    if (validate_plan(plan, w) != RIP_OK) return RIP_EINVAL;
+    bool any = false;
+    for (uint64_t n : ns) any |= n > 1;
+    ds->last_info[0] = ds->last_info[1] = ds->last_info[2] = 0;
+    if (!any) return RIP_OK;
+
+    const Layout lay = make_layout(ns, w, plan);
+    char* wsp = static_cast<char*>(ws);
+    if (wsp) {
+        if (ws_bytes < lay.total || (reinterpret_cast<uintptr_t>(wsp) & 255)) return RIP_EWORKSPACE;
+    } else {
+        std::lock_guard<std::mutex> lock(g_mutex);
+        if (ds->ws_bytes < lay.total) {
+            if (ds->ws) {
+                cudaDeviceSynchronize();
+                cudaFree(ds->ws);
+                ds->ws = nullptr;
+                ds->ws_bytes = 0;
+            }
+            if (cudaMalloc(&ds->ws, lay.total) != cudaSuccess) {
+                cudaGetLastError();
+                return RIP_ENOMEM;
+            }
+            ds->ws_bytes = lay.total;
+        }
+        wsp = static_cast<char*>(ds->ws);
+    }
+    ds->last_info[0] = lay.aux_bytes;
+
+    const DevPlan dplan = to_dev(plan);
+    uint32_t bmin = 0xffffffffu;
+    for (uint32_t l = 0; l < plan.num_levels; ++l) bmin = std::min(bmin, plan.level[l].block);
+    // array table: device pointer, size, seed, slot base
+    std::vector<ArrayDesc> arr(ptrs.size());
+    uint64_t slot = 0;
+    bool aligned16 = true;
+    for (size_t i = 0; i < ptrs.size(); ++i) {
+        arr[i] = ArrayDesc{ptrs[i], ns[i] > 1 ? ns[i] : 0, base_seed + i, slot};
+        slot += (ns[i] + bmin - 1) / bmin;
+        aligned16 &= (reinterpret_cast<uintptr_t>(ptrs[i]) % 16) == 0;
+    }
+    ArrayDesc* d_arr = reinterpret_cast<ArrayDesc*>(wsp + lay.arrays);
+    if (cudaMemcpyAsync(d_arr, arr.data(), sizeof(ArrayDesc) * arr.size(), cudaMemcpyHostToDevice, stream) !=
+        cudaSuccess)
+        return RIP_ECUDA;
+
+    uint32_t* counts = reinterpret_cast<uint32_t*>(wsp + lay.counts);
+    Lists lists{};
+    lists.big[0] = reinterpret_cast<Sub*>(wsp + lay.lists_big0);
+    lists.big[1] = reinterpret_cast<Sub*>(wsp + lay.lists_big1);
+    lists.big_count[0] = counts + 0;
+    lists.big_count[1] = counts + 1;
+    lists.big_cap = lay.big_cap;
+    lists.small = reinterpret_cast<Sub*>(wsp + lay.small);
+    lists.small_count = counts + 2;
+    lists.medium = reinterpret_cast<Sub*>(wsp + lay.medium);
+    lists.medium_count = counts + 3;
+    lists.small_cap = lay.small_cap;
+    lists.bigfy = reinterpret_cast<Sub*>(wsp + lay.bigfy);
+    lists.bigfy_count = counts + 4;
+    lists.bigfy_cap = lay.bigfy_cap;
+
+    uint32_t* counters = reinterpret_cast<uint32_t*>(wsp + lay.counters);
+    uint64_t* pool_used = reinterpret_cast<uint64_t*>(wsp + lay.pool_used);
+    uint32_t launches = 0;
+
+    InitArgs ia{d_arr, (uint32_t)arr.size(), dplan, ds->status, lists, lay.small_max_m, counters, pool_used};
+    if (launch_init(ia, stream) != cudaSuccess) return RIP_ECUDA;
+    ++launches;
+
+    auto run_small = [&]() -> int {
+        SmallArgs sa{lists.small, lists.small_count, lists.small_cap, d_arr, dplan, ds->status, nullptr, 0, 0};
+        const size_t smem = small_smem_bytes(lay.small_max_m, w, false);
+        if (launch_small(sa, w, smem, ds->num_sms, stream) != cudaSuccess) return RIP_ECUDA;
+        SmallArgs ma{lists.medium, lists.medium_count, lists.small_cap, d_arr, dplan, ds->status,
+                     wsp + lay.mscratch, (uint64_t)kMediumMaxM * w, 1};
+        const size_t msmem = small_smem_bytes(kMediumMaxM, w, true);
+        if (launch_small(ma, w, msmem, kMediumGrid, stream) != cudaSuccess) return RIP_ECUDA;
+        launches += 2;
+        return RIP_OK;
+    };
+    int rc = run_small();
+    if (rc) return rc;
+
+    for (uint32_t lev = 0; lev < lay.levels; ++lev) {
+        const uint32_t li = dplan.idx(lev);
+        LevelArgs a{};
+        a.arrays = d_arr;
+        a.plan = dplan;
+        a.status = ds->status;
+        a.level = lev;
+        a.k = plan.level[li].k;
+        a.B = plan.level[li].block;
+        a.T = plan.level[li].tile;
+        a.vec16 = aligned16 && ((a.B * w) % 16 == 0) ? 1u : 0u;
+        a.big = lists.big[lev & 1];
+        a.big_count = lists.big_count[lev & 1];
+        a.next_big = lists.big[(lev + 1) & 1];
+        a.next_big_count = lists.big_count[(lev + 1) & 1];
+        a.big_cap = lay.big_cap;
+        a.small = lists.small;
+        a.small_count = lists.small_count;
+        a.medium = lists.medium;
+        a.medium_count = lists.medium_count;
+        a.small_cap = lay.small_cap;
+        a.bigfy = lists.bigfy;
+        a.bigfy_count = lists.bigfy_count;
+        a.bigfy_cap = lay.bigfy_cap;
+        a.small_max_m = lay.small_max_m;
+        a.tiles = reinterpret_cast<TileRef*>(wsp + lay.tiles);
+        a.sp_tile_begin = reinterpret_cast<uint32_t*>(wsp + lay.sp_tile_begin);
+        a.counters = counters;
+        a.pool_used = pool_used;
+        a.tile_cap = lay.tile_cap;
+        a.C = reinterpret_cast<uint32_t*>(wsp + lay.C);
+        a.FBc = reinterpret_cast<uint32_t*>(wsp + lay.FBc);
+        a.TLc = reinterpret_cast<uint32_t*>(wsp + lay.TLc);
+        a.tinfo = reinterpret_cast<TileInfo*>(wsp + lay.tinfo);
+        a.cand_prefix = reinterpret_cast<uint64_t*>(wsp + lay.cand_prefix);
+        a.child = reinterpret_cast<ChildInfo*>(wsp + lay.child);
+        a.words = reinterpret_cast<uint32_t*>(wsp + lay.words);
+        a.pool = wsp + lay.pool;
+        a.pool_cap = lay.pool_cap;
+        a.dem = reinterpret_cast<DemRec*>(wsp + lay.dem);
+        a.dem_cap = lay.dem_cap;
+        if (launch_level(a, w, ds->num_sms, stream, &launches) != cudaSuccess) return RIP_ECUDA;
+        rc = run_small();
+        if (rc) return rc;
+    }
+    if (launch_bigfy(lists.bigfy, lists.bigfy_count, lists.bigfy_cap, d_arr, dplan, w,
+                     lists.big_count[lay.levels & 1], ds->status, stream) != cudaSuccess)
+        return RIP_ECUDA;
+    ++launches;
+    ds->last_info[1] = lay.levels;
+    ds->last_info[2] = launches;
+    return RIP_OK;
+}
+
+}  // namespace
+}  // namespace rip
+
+using namespace rip;
+
+extern "C" {
+
+int rip_default_plan(uint64_t n, uint32_t elem_bytes, rip_plan* plan) {
+    if (!plan || !valid_w(elem_bytes)) return RIP_EINVAL;
+    DevState* ds = dev_state(nullptr);
+    return default_plan_impl(n, elem_bytes, plan, ds ? ds->num_sms : 152) ? RIP_OK : RIP_EINVAL;
+}
+
+size_t rip_shuffle_workspace_size(uint64_t n, uint32_t elem_bytes, const rip_plan* plan) {
+    uint64_t one = n;
+    return rip_shuffle_batched_workspace_size(&one, 1, elem_bytes, plan);
+}
+
+size_t rip_shuffle_batched_workspace_size(const uint64_t* ns, uint32_t count, uint32_t elem_bytes,
+                                          const rip_plan* plan) {
+    if (!valid_w(elem_bytes) || (count && !ns)) return 0;
+    std::vector<uint64_t> v(ns, ns + count);
+    uint64_t nmax = 0;
+    for (uint64_t n : v) nmax = std::max(nmax, n);
+    rip_plan p;
+    if (plan) p = *plan;
+    else {
+        DevState* ds = dev_state(nullptr);
+        default_plan_impl(nmax, elem_bytes, &p, ds ? ds->num_sms : 152);
+    }
+    if (validate_plan(p, elem_bytes) != RIP_OK) return 0;
+    return make_layout(v, elem_bytes, p).total;
+}
+
+int rip_shuffle(void* data, uint64_t n, uint32_t elem_bytes, uint64_t seed, rip_stream_t stream) {
+    return rip_shuffle_ex(data, n, elem_bytes, seed, nullptr, nullptr, 0, stream);
+}
+
+int rip_shuffle_ex(void* data, uint64_t n, uint32_t elem_bytes, uint64_t seed, const rip_plan* plan, void* ws,
+                   size_t ws_bytes, rip_stream_t stream) {
+    std::vector<char*> p{static_cast<char*>(data)};
+    std::vector<uint64_t> ns{n};
+    return run_shuffle(p, ns, elem_bytes, seed, plan, ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int rip_shuffle_batched(void* const* ptrs, const uint64_t* ns, uint32_t count, uint32_t elem_bytes,
+                        uint64_t base_seed, const rip_plan* plan, void* ws, size_t ws_bytes, rip_stream_t stream) {
+    if (count && (!ptrs || !ns)) return RIP_EINVAL;
+    std::vector<char*> p(count);
+    std::vector<uint64_t> n(ns, ns + count);
+    for (uint32_t i = 0; i < count; ++i) p[i] = static_cast<char*>(ptrs[i]);
+    return run_shuffle(p, n, elem_bytes, base_seed, plan, ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int rip_digest(const void* data, uint64_t n, uint32_t elem_bytes, uint64_t* out, rip_stream_t stream) {
+    if (!out || !valid_w(elem_bytes) || (n && !data)) return RIP_EINVAL;
+    DevState* ds = dev_state(nullptr);
+    if (!ds) return RIP_ECUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    {
+        std::lock_guard<std::mutex> lock(g_mutex);
+        if (!ds->digest_buf && cudaMalloc(&ds->digest_buf, sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            return RIP_ENOMEM;
+        }
+    }
+    if (cudaMemsetAsync(ds->digest_buf, 0, sizeof(unsigned long long), s) != cudaSuccess) return RIP_ECUDA;
+    if (n && launch_digest(data, n, elem_bytes, ds->digest_buf, s) != cudaSuccess) return RIP_ECUDA;
+    unsigned long long h = 0;
+    if (cudaMemcpyAsync(&h, ds->digest_buf, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RIP_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return RIP_ECUDA;
+    *out = h;
+    return RIP_OK;
+}
+
+int rip_get_device_status(rip_stream_t stream) {
+    DevState* ds = dev_state(nullptr);
+    if (!ds) return RIP_ECUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return RIP_ECUDA;
+    Status st{};
+    if (cudaMemcpy(&st, ds->status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return RIP_ECUDA;
+    if (st.code) {
+        Status zero{};
+        if (cudaMemcpy(ds->status, &zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess) return RIP_ECUDA;
+    }
+    return (int)st.code;
+}
+
+int rip_release_workspace(void) {
+    DevState* ds = dev_state(nullptr);
+    if (!ds) return RIP_ECUDA;
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (ds->ws) {
+        if (cudaDeviceSynchronize() != cudaSuccess) return RIP_ECUDA;
+        cudaFree(ds->ws);
+        ds->ws = nullptr;
+        ds->ws_bytes = 0;
+    }
+    return RIP_OK;
+}
+
+const char* rip_strerror(int code) {
+    switch (code) {
+        case RIP_OK: return "ok";
+        case RIP_EINVAL: return "invalid argument or plan";
+        case RIP_ENOMEM: return "device workspace allocation failed";
+        case RIP_EWORKSPACE: return "workspace too small or device pool exhausted";
+        case RIP_ECUDA: return "CUDA runtime error";
+        case RIP_ETIMEOUT: return "device-side wait limit expired";
+        case RIP_EINTERNAL: return "device-side consistency check failed";
+        default: return "unknown error";
+    }
+}
+
+int rip_last_call_info(uint64_t out[3]) {
+    if (!out) return RIP_EINVAL;
+    DevState* ds = dev_state(nullptr);
+    if (!ds) return RIP_ECUDA;
+    for (int i = 0; i < 3; ++i) out[i] = ds->last_info[i];
+    return RIP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,161 @@
+// rip_internal.cuh -- kernel argument blocks and launch entry points shared
+// by the translation units of the library.
+#pragma once
+#include "rip_device.cuh"
+
+namespace rip {
+
+constexpr uint32_t kMaxK = 1024;
+constexpr uint32_t kSmallThreads = 1024;
+constexpr uint32_t kSmallCntCap = 512;    // (tile, bucket) counters of one in-SMEM scatter
+constexpr uint32_t kSmallTbl = 4096;      // (ranking warp, bucket) entries
+constexpr uint32_t kSmallStack = 256;     // pending scatter ranges inside one subproblem
+constexpr uint32_t kMediumMaxM = 49152;   // largest subproblem finished on one SM
+constexpr uint32_t kClassifyThreads = 512;
+constexpr uint32_t kClsTbl = 4096;
+constexpr uint32_t kPermuteThreads = 256;
+constexpr uint32_t kGroup = 8;            // lanes moving one block in the permutation
+constexpr size_t kSmemOptin = 232448;     // dynamic shared memory per block on sm_100/103
+
+// Slot words (one per B-element slot of the array):
+//   bits 31..30 state: 00 empty, 01 holds an unmoved block, 11 claimed, 10 filled
+//   after classification: bits 29..20 bucket, 19..0 block index inside (tile, bucket)
+//   after resolution:     bit 29 "goes to the pool", bits 28..0 destination slot
+//                         (or demoted-record index when bit 29 is set)
+constexpr uint32_t kWordOcc = 1u << 30;
+constexpr uint32_t kWordTaken = 1u << 31;
+constexpr uint32_t kWordDem = 1u << 29;
+constexpr uint32_t kWordDestMask = (1u << 29) - 1u;
+constexpr uint32_t kBlkBits = 20;
+
+struct TileRef {
+    uint32_t sp;  // index in the level's big list
+    uint32_t t;   // tile index inside the subproblem
+};
+
+struct TileInfo {
+    uint64_t hs0;        // slot-table index of the tile's first home slot
+    uint64_t pool_base;  // element offset of the tile's tails in the pool
+    uint32_t home_used;  // home slots holding a full block after classification
+    uint32_t H;          // home slots available
+};
+
+struct ChildInfo {
+    uint64_t o;          // region start (array-relative)
+    uint64_t m;          // size
+    uint64_t slot_base;  // slot-table index of full block 0
+    uint32_t Fb;         // full blocks of the bucket
+    uint32_t placed;     // full blocks that go to slots (Fb or Fb-1)
+    uint32_t eps;        // rotation of the child region
+    uint32_t pad;
+};
+
+struct DemRec {
+    uint32_t sp, tile, b, blk;
+    uint64_t pool_off;
+};
+
+struct Lists {
+    Sub* big[2];
+    uint32_t* big_count[2];
+    uint32_t big_cap;
+    Sub* small;
+    uint32_t* small_count;
+    Sub* medium;
+    uint32_t* medium_count;
+    uint32_t small_cap;
+    Sub* bigfy;
+    uint32_t* bigfy_count;
+    uint32_t bigfy_cap;
+};
+
+struct LevelArgs {
+    const ArrayDesc* arrays;
+    DevPlan plan;
+    Status* status;
+    uint32_t level, k, B, vec16;
+    uint64_t T;
+    // this level's subproblems and the next level's
+    const Sub* big;
+    const uint32_t* big_count;
+    Sub* next_big;
+    uint32_t* next_big_count;
+    uint32_t big_cap;
+    Sub* small;
+    uint32_t* small_count;
+    Sub* medium;
+    uint32_t* medium_count;
+    uint32_t small_cap;
+    Sub* bigfy;
+    uint32_t* bigfy_count;
+    uint32_t bigfy_cap;
+    uint32_t small_max_m;  // largest m whose data fits in shared memory
+    // tiles
+    TileRef* tiles;
+    uint32_t* sp_tile_begin;  // per big subproblem
+    uint32_t* counters;       // [0] tiles, [1] tile cursor, [2] demoted count, [4..5] candidate cursor
+    uint64_t* pool_used;
+    uint32_t tile_cap;
+    uint32_t* C;    // tile_cap x k counts
+    uint32_t* FBc;  // tile_cap x k full blocks of earlier tiles
+    uint32_t* TLc;  // tile_cap x k tail elements of earlier tiles
+    TileInfo* tinfo;
+    uint64_t* cand_prefix;  // tile_cap + 1
+    ChildInfo* child;       // big_cap x k
+    uint32_t* words;
+    char* pool;
+    uint64_t pool_cap;  // elements
+    DemRec* dem;
+    uint32_t dem_cap;
+};
+
+struct SmallArgs {
+    const Sub* list;
+    const uint32_t* count;
+    uint32_t capacity;
+    const ArrayDesc* arrays;
+    DevPlan plan;
+    Status* status;
+    char* gscratch;
+    uint64_t gslot_bytes;
+    uint32_t medium;
+};
+
+struct InitArgs {
+    const ArrayDesc* arrays;
+    uint32_t narrays;
+    DevPlan plan;
+    Status* status;
+    Lists lists;
+    uint32_t small_max_m;
+    uint32_t* counters;
+    uint64_t* pool_used;
+};
+
+// rip_small.cu
+size_t small_fixed_smem();
+size_t small_smem_bytes(uint64_t m, uint32_t w, bool medium);
+cudaError_t launch_small(const SmallArgs& args, uint32_t w, size_t smem, uint32_t grid, cudaStream_t stream);
+
+// rip_level.cu
+size_t classify_smem_bytes(uint32_t k, uint32_t B, uint32_t w);
+size_t permute_smem_bytes(uint32_t B, uint32_t w);
+cudaError_t launch_init(const InitArgs& a, cudaStream_t s);
+cudaError_t launch_level(const LevelArgs& a, uint32_t w, uint32_t num_sms, cudaStream_t s, uint32_t* launches);
+cudaError_t launch_bigfy(const Sub* list, const uint32_t* count, uint32_t cap, const ArrayDesc* arrays,
+                         DevPlan plan, uint32_t w, const uint32_t* leftover, Status* status, cudaStream_t s);
+
+// rip_digest.cu
+cudaError_t launch_digest(const void* data, uint64_t n, uint32_t w, unsigned long long* out, cudaStream_t s);
+
+// device-side eligibility of a subproblem for the on-SM solver (same rule as the host's)
+__device__ __host__ __forceinline__ bool small_solver_can_scatter(const DevPlan& plan, uint64_t m, uint32_t L) {
+    for (uint32_t l = plan.idx(L); l < plan.num_levels; ++l) {
+        const uint64_t T = plan.T[l];
+        const uint64_t tiles = T >= m ? 1 : (m + T - 1) / T;
+        if (tiles * plan.k[l] > kSmallCntCap || plan.k[l] > kMaxK) return false;
+    }
+    return true;
+}
+
+}  // namespace rip

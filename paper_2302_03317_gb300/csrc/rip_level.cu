@@ -1,0 +1,824 @@
+// rip_level.cu -- one in-place scatter level over all large subproblems.
+//
+// The level computes the canonical layout of one ScatterShuffle level
+// (Sec. 2.2; the in-place IpSc contract of Sec. 3.1 and Sec. 3.5: bucket b
+// becomes a contiguous region) for every subproblem too large for one SM:
+//
+//  tiles     build the level's tile list (T elements per tile, per subproblem)
+//  classify  one CTA streams one tile: Philox bucket draws, stable ranks per
+//            bucket (warp match_any + per-warp counts), B-element bucket
+//            buffers in shared memory; every completed block is written back
+//            into the tile's own, already-read front ("home slots"); the
+//            partial buffers (the tails) go to a small pool
+//  scan      per subproblem: bucket sizes, region starts, per-(tile, bucket)
+//            prefix of full blocks and tails, child descriptors and rotations
+//  resolve   turn each home slot's (bucket, block) into its destination slot
+//  permute   move every block to its destination in place by following the
+//            slot permutation; 8 lanes move one block, slots are claimed with
+//            atomics (claim, read, then write), chains start anywhere
+//  tails     write the tails (and the few blocks that straddle a region end)
+//            from the pool to their final positions
+//
+// Children are stored rotated: logical index i of a child region lives at
+// physical o + ((i + eps) mod m), eps chosen so that the child's full blocks
+// sit on the B-aligned slot grid; every later reader goes through the rotation
+// and the last one (the on-SM solver) writes canonical order.
+#include "rip_internal.cuh"
+
+namespace rip {
+
+namespace {
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ uint32_t atom_or_acqrel(uint32_t* p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.acq_rel.gpu.global.or.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+template <typename U>
+__device__ __forceinline__ U ld_cg(const U* p) {
+    return __ldcg(p);
+}
+
+__device__ __forceinline__ bool push_sub(Sub* list, uint32_t* count, uint32_t cap, const Sub& s, Status* st,
+                                         uint32_t where) {
+    const uint32_t i = atomicAdd(count, 1u);
+    if (i < cap) {
+        list[i] = s;
+        return true;
+    }
+    report(st, RIP_EWORKSPACE, where, i);
+    return false;
+}
+
+// Route a subproblem to the list that will process it.
+__device__ void route_sub(const Sub& c, const DevPlan& plan, uint32_t small_max_m, Sub* next_big,
+                          uint32_t* next_big_count, uint32_t big_cap, Sub* small, uint32_t* small_count,
+                          Sub* medium, uint32_t* medium_count, uint32_t small_cap, Sub* bigfy,
+                          uint32_t* bigfy_count, uint32_t bigfy_cap, Status* st) {
+    if (c.m <= 1) return;
+    const bool leaf = plan.is_leaf(c.m, c.level);
+    const bool solver_ok = leaf || small_solver_can_scatter(plan, c.m, c.level);
+    if (c.m <= small_max_m && solver_ok)
+        push_sub(small, small_count, small_cap, c, st, 0x6001);
+    else if (c.m <= kMediumMaxM && solver_ok)
+        push_sub(medium, medium_count, small_cap, c, st, 0x6002);
+    else if (leaf)
+        push_sub(bigfy, bigfy_count, bigfy_cap, c, st, 0x6003);
+    else
+        push_sub(next_big, next_big_count, big_cap, c, st, 0x6004);
+}
+
+// ------------------------------------------------------------------ init
+
+__global__ void init_kernel(InitArgs a) {
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid == 0) {
+        *a.lists.big_count[0] = 0;
+        *a.lists.big_count[1] = 0;
+        *a.lists.small_count = 0;
+        *a.lists.medium_count = 0;
+        *a.lists.bigfy_count = 0;
+        for (int i = 0; i < 8; ++i) a.counters[i] = 0;
+        *a.pool_used = 0;
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < a.narrays; i += gridDim.x * blockDim.x) {
+        const ArrayDesc ad = a.arrays[i];
+        Sub s{0, ad.n, i, 0, 0, 0};
+        route_sub(s, a.plan, a.small_max_m, a.lists.big[0], a.lists.big_count[0], a.lists.big_cap,
+                  a.lists.small, a.lists.small_count, a.lists.medium, a.lists.medium_count, a.lists.small_cap,
+                  a.lists.bigfy, a.lists.bigfy_count, a.lists.bigfy_cap, a.status);
+    }
+}
+
+// ------------------------------------------------------------------ tiles
+
+__global__ void tiles_kernel(LevelArgs a) {
+    __shared__ uint32_t scan[32];
+    __shared__ uint32_t carry;
+    const uint32_t nbig = min(*a.big_count, a.big_cap);
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < nbig; c0 += blockDim.x) {
+        const uint32_t sp = c0 + threadIdx.x;
+        uint32_t nt = 0;
+        if (sp < nbig) {
+            const uint64_t m = a.big[sp].m;
+            const uint64_t t64 = a.T >= m ? 1 : (m + a.T - 1) / a.T;
+            nt = (uint32_t)(t64 < 0xffffffffull ? t64 : 0xffffffffull);
+        }
+        uint32_t total;
+        const uint32_t ex = block_exclusive_scan<uint32_t>(nt, scan, &total);
+        const uint32_t begin = carry + ex;
+        if (sp < nbig) {
+            a.sp_tile_begin[sp] = begin;
+            for (uint32_t t = 0; t < nt; ++t)
+                if (begin + t < a.tile_cap) a.tiles[begin + t] = TileRef{sp, t};
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (carry > a.tile_cap) report(a.status, RIP_EWORKSPACE, 0x6101, carry);
+        a.counters[0] = min(carry, a.tile_cap);
+        a.counters[1] = 0;
+        a.counters[2] = 0;
+        a.counters[3] = 0;
+        a.counters[4] = 0;
+        a.counters[5] = 0;
+        *a.pool_used = 0;
+        *a.next_big_count = 0;
+        *a.small_count = 0;
+        *a.medium_count = 0;
+    }
+}
+
+// ------------------------------------------------------------------ classify
+
+struct ClsShared {
+    uint32_t run[kMaxK];      // bucket elements seen in this tile
+    uint32_t newrun[kMaxK];   // ... after the current round
+    uint32_t hsb[kMaxK];      // home index of the first block completing this round
+    uint32_t dfirst[kMaxK];   // first home index that is demoted, per bucket (this round)
+    uint64_t dbase[kMaxK];    // pool offset of that demoted block
+    uint16_t tbl[kClsTbl];    // (ranking warp, bucket) counts of the round
+    uint16_t flist[kMaxK];    // buckets whose buffered block completes this round
+    uint32_t scan[32];
+    uint32_t nflush;
+    uint32_t home_next;
+    uint32_t tile;
+    uint32_t pad;
+    uint64_t pool_base;
+};
+
+template <int W, int E>
+__global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs a) {
+    using T = typename Elem<W>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ClsShared& sh = *reinterpret_cast<ClsShared*>(smem_raw);
+    T* buf = reinterpret_cast<T*>(smem_raw + ((sizeof(ClsShared) + 15) & ~size_t(15)));
+    const uint32_t k = a.k, B = a.B, L = a.level;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t nwarps = blockDim.x >> 5;
+    const uint32_t nwr = min(nwarps, kClsTbl / k);
+    const uint32_t round = nwr * 32u * E;
+    const uint32_t ntiles = a.counters[0];
+    const uint32_t lt_mask = (1u << lane) - 1u;
+
+    for (;;) {
+        if (tid == 0) sh.tile = atomicAdd(&a.counters[1], 1u);
+        __syncthreads();
+        const uint32_t tile = sh.tile;
+        if (tile >= ntiles) break;
+        const TileRef tr = a.tiles[tile];
+        const Sub S = a.big[tr.sp];
+        const ArrayDesc ad = a.arrays[S.arr];
+        T* base = reinterpret_cast<T*>(ad.data);
+        const PhiloxKey key = make_key(ad.seed);
+        const uint64_t lo = (uint64_t)tr.t * a.T;
+        const uint32_t r = (uint32_t)(min(lo + a.T, S.m) - lo);
+        const uint64_t alo = S.o + S.eps + lo;  // physical start of the tile's aligned piece
+        const uint64_t avail = S.m > S.eps + lo ? min((uint64_t)r, S.m - S.eps - lo) : 0;
+        const uint32_t H = (uint32_t)(avail / B);
+        const uint64_t hs0 = ad.slot_base + alo / B;
+        if (alo % B != 0 && tid == 0) report(a.status, RIP_EINTERNAL, 0x6201, alo);
+
+        for (uint32_t b = tid; b < k; b += blockDim.x) sh.run[b] = 0;
+        for (uint32_t j = tid; j < nwr * k; j += blockDim.x) sh.tbl[j] = 0;
+        if (tid == 0) {
+            sh.home_next = 0;
+            sh.nflush = 0;
+        }
+        T val[E], nxt[E];
+        if (warp < nwr) {
+#pragma unroll
+            for (uint32_t e = 0; e < E; ++e) {
+                const uint32_t i = (warp * E + e) * 32u + lane;
+                if (i < r) nxt[e] = base[phys_index(S, lo + i)];
+            }
+        }
+        __syncthreads();
+
+        for (uint32_t R = 0; R < r; R += round) {
+            uint32_t bb[E], rk[E];
+            if (warp < nwr) {
+#pragma unroll
+                for (uint32_t e = 0; e < E; ++e) val[e] = nxt[e];
+                if (R + round < r) {
+#pragma unroll
+                    for (uint32_t e = 0; e < E; ++e) {
+                        const uint32_t i = R + round + (warp * E + e) * 32u + lane;
+                        if (i < r) nxt[e] = base[phys_index(S, lo + i)];
+                    }
+                }
+#pragma unroll
+                for (uint32_t e = 0; e < E; ++e) {
+                    const uint32_t ib = R + (warp * E + e) * 32u;
+                    const bool valid = ib + lane < r;
+                    const uint32_t word = warp_scatter_word(key, L, S.o, S.o + lo + ib);
+                    const uint32_t b = bucket_of(word, k);
+                    const uint32_t kk = valid ? b : 0xffffffffu;
+                    const uint32_t peers = __match_any_sync(0xffffffffu, kk);
+                    const uint32_t pre = valid ? sh.tbl[warp * k + b] : 0u;
+                    __syncwarp();
+                    if (valid && lane == (uint32_t)(__ffs(peers) - 1))
+                        sh.tbl[warp * k + b] = (uint16_t)(pre + __popc(peers));
+                    __syncwarp();
+                    bb[e] = valid ? b : 0xffffffffu;
+                    rk[e] = pre + __popc(peers & lt_mask);
+                }
+            }
+            __syncthreads();
+
+            // per-bucket bookkeeping: completed blocks, home slots, demotion
+            for (uint32_t b = tid; b < k; b += blockDim.x) {
+                uint32_t tot = 0;
+                for (uint32_t w = 0; w < nwr; ++w) tot += sh.tbl[w * k + b];
+                const uint32_t rb = sh.run[b], nr = rb + tot;
+                sh.newrun[b] = nr;
+                const uint32_t cb = rb / B, eb = nr / B;
+                if (eb > cb) {
+                    const uint32_t nb = eb - cb;
+                    const uint32_t hs = atomicAdd(&sh.home_next, nb);
+                    sh.hsb[b] = hs;
+                    const uint32_t first_dem = max(hs, H);
+                    const uint32_t ndem = hs + nb > first_dem ? hs + nb - first_dem : 0;
+                    uint64_t pool_off = 0;
+                    if (ndem) {
+                        pool_off = atomicAdd((unsigned long long*)a.pool_used, (unsigned long long)ndem * B);
+                        if (pool_off + (uint64_t)ndem * B > a.pool_cap) report(a.status, RIP_EWORKSPACE, 0x6202, pool_off);
+                        sh.dfirst[b] = first_dem;
+                        sh.dbase[b] = pool_off;
+                    }
+                    for (uint32_t j = 0; j < nb; ++j) {
+                        const uint32_t h = hs + j, blk = cb + j;
+                        if (blk >= (1u << kBlkBits)) report(a.status, RIP_EINVAL, 0x6203, blk);
+                        if (h < H) {
+                            a.words[hs0 + h] = kWordOcc | (b << kBlkBits) | blk;
+                        } else {
+                            const uint32_t rec = atomicAdd(&a.counters[2], 1u);
+                            if (rec < a.dem_cap)
+                                a.dem[rec] = DemRec{tr.sp, tile, b, blk, pool_off + (uint64_t)(h - first_dem) * B};
+                            else
+                                report(a.status, RIP_EWORKSPACE, 0x6204, rec);
+                        }
+                    }
+                    if (rb % B != 0) sh.flist[atomicAdd(&sh.nflush, 1u)] = (uint16_t)b;
+                }
+            }
+            __syncthreads();
+
+            // phase 1: elements of blocks completing in this round
+            if (warp < nwr) {
+#pragma unroll
+                for (uint32_t e = 0; e < E; ++e) {
+                    const uint32_t b = bb[e];
+                    if (b == 0xffffffffu) continue;
+                    uint32_t cross = 0;
+                    for (uint32_t w = 0; w < warp; ++w) cross += sh.tbl[w * k + b];
+                    const uint32_t rb = sh.run[b];
+                    const uint32_t rank = rb + cross + rk[e];
+                    rk[e] = rank;
+                    const uint32_t blk = rank / B, pos = rank - blk * B;
+                    const uint32_t cb = rb / B, eb = sh.newrun[b] / B;
+                    if (blk < eb) {
+                        if (blk == cb && rb % B != 0) {
+                            buf[b * B + pos] = val[e];
+                        } else {
+                            const uint32_t h = sh.hsb[b] + (blk - cb);
+                            const uint64_t poff = sh.dbase[b] + (uint64_t)(h - sh.dfirst[b]) * B;
+                            if (h >= H && poff + B > a.pool_cap) continue;  // reported at allocation
+                            T* dst = h < H ? base + alo + (uint64_t)h * B : reinterpret_cast<T*>(a.pool) + poff;
+                            dst[pos] = val[e];
+                        }
+                        bb[e] = 0xffffffffu;  // placed
+                    }
+                }
+            }
+            __syncthreads();
+
+            // flush the buffered blocks that completed
+            {
+                const uint32_t nf = sh.nflush;
+                for (uint32_t f = warp; f < nf; f += nwarps) {
+                    const uint32_t b = sh.flist[f];
+                    const uint32_t h = sh.hsb[b];
+                    const uint64_t poff = sh.dbase[b] + (uint64_t)(h - sh.dfirst[b]) * B;
+                    if (h >= H && poff + B > a.pool_cap) continue;  // reported at allocation
+                    T* dst = h < H ? base + alo + (uint64_t)h * B : reinterpret_cast<T*>(a.pool) + poff;
+                    const T* src = buf + b * B;
+                    if (a.vec16 && W < 16) {
+                        const uint32_t units = B * W / 16u;
+                        for (uint32_t u = lane; u < units; u += 32u)
+                            reinterpret_cast<uint4*>(dst)[u] = reinterpret_cast<const uint4*>(src)[u];
+                    } else {
+                        for (uint32_t u = lane; u < B; u += 32u) dst[u] = src[u];
+                    }
+                }
+            }
+            __syncthreads();
+
+            // phase 2: elements that start the next partial block
+            if (warp < nwr) {
+#pragma unroll
+                for (uint32_t e = 0; e < E; ++e) {
+                    const uint32_t b = bb[e];
+                    if (b == 0xffffffffu) continue;
+                    buf[b * B + rk[e] % B] = val[e];
+                }
+            }
+            __syncthreads();
+            for (uint32_t b = tid; b < k; b += blockDim.x) {
+                sh.run[b] = sh.newrun[b];
+                for (uint32_t w = 0; w < nwr; ++w) sh.tbl[w * k + b] = 0;
+            }
+            if (tid == 0) sh.nflush = 0;
+            __syncthreads();
+        }
+
+        // tails of every bucket -> pool; counts and tile info
+        {
+            const uint32_t i0 = 2 * tid, i1 = 2 * tid + 1;
+            const uint32_t r0 = i0 < k ? sh.run[i0] % B : 0, r1 = i1 < k ? sh.run[i1] % B : 0;
+            uint32_t total;
+            const uint32_t ex = block_exclusive_scan<uint32_t>(r0 + r1, sh.scan, &total);
+            if (i0 < k) sh.hsb[i0] = ex;
+            if (i1 < k) sh.hsb[i1] = ex + r0;
+            if (tid == 0) {
+                const uint64_t pb = atomicAdd((unsigned long long*)a.pool_used, (unsigned long long)total);
+                if (pb + total > a.pool_cap) report(a.status, RIP_EWORKSPACE, 0x6205, pb);
+                sh.pool_base = pb;
+            }
+            __syncthreads();
+            const uint64_t pb = sh.pool_base;
+            if (pb + total <= a.pool_cap) {
+                T* pool = reinterpret_cast<T*>(a.pool);
+                for (uint32_t b = warp; b < k; b += nwarps) {
+                    const uint32_t R = sh.run[b] % B;
+                    for (uint32_t j = lane; j < R; j += 32u) pool[pb + sh.hsb[b] + j] = buf[b * B + j];
+                }
+            }
+            for (uint32_t b = tid; b < k; b += blockDim.x) a.C[(uint64_t)tile * k + b] = sh.run[b];
+            const uint32_t used = min(sh.home_next, H);
+            for (uint32_t h = used + tid; h < H; h += blockDim.x) a.words[hs0 + h] = 0u;
+            if (tid == 0) a.tinfo[tile] = TileInfo{hs0, pb, used, H};
+            __syncthreads();
+        }
+    }
+}
+
+// ------------------------------------------------------------------ scan
+
+__global__ void scan_kernel(LevelArgs a, uint32_t small_max_m) {
+    __shared__ uint64_t start[kMaxK];
+    __shared__ uint64_t scan64[32];
+    const uint32_t k = a.k, B = a.B;
+    const uint32_t nbig = min(*a.big_count, a.big_cap);
+    for (uint32_t sp = blockIdx.x; sp < nbig; sp += gridDim.x) {
+        const Sub S = a.big[sp];
+        const ArrayDesc ad = a.arrays[S.arr];
+        const uint32_t nt = (uint32_t)(a.T >= S.m ? 1 : (S.m + a.T - 1) / a.T);
+        const uint32_t tb = a.sp_tile_begin[sp];
+        for (uint32_t b = threadIdx.x; b < k; b += blockDim.x) {
+            uint64_t size = 0;
+            uint32_t fsum = 0, rsum = 0;
+            for (uint32_t t = 0; t < nt; ++t) {
+                const uint64_t ci = (uint64_t)(tb + t) * k + b;
+                const uint32_t c = a.C[ci];
+                a.FBc[ci] = fsum;
+                a.TLc[ci] = rsum;
+                fsum += c / B;
+                rsum += c % B;
+                size += c;
+            }
+            start[b] = size;
+            ChildInfo ci{};
+            ci.Fb = fsum;
+            ci.placed = rsum;  // tails, temporarily
+            a.child[(uint64_t)sp * k + b] = ci;
+        }
+        __syncthreads();
+        {
+            const uint32_t i0 = 2 * threadIdx.x, i1 = 2 * threadIdx.x + 1;
+            const uint64_t v0 = i0 < k ? start[i0] : 0, v1 = i1 < k ? start[i1] : 0;
+            const uint64_t ex = block_exclusive_scan<uint64_t>(v0 + v1, scan64, nullptr);
+            if (i0 < k) start[i0] = ex;
+            if (i1 < k) start[i1] = ex + v0;
+        }
+        __syncthreads();
+        for (uint32_t b = threadIdx.x; b < k; b += blockDim.x) {
+            ChildInfo ci = a.child[(uint64_t)sp * k + b];
+            const uint32_t tails = ci.placed;
+            const uint64_t sb = start[b];
+            const uint64_t se = b + 1 < k ? start[b + 1] : S.m;
+            ci.o = S.o + sb;
+            ci.m = se - sb;
+            const uint32_t e0 = (uint32_t)((B - ci.o % B) % B);
+            ci.eps = ci.m > e0 ? e0 : 0;
+            ci.placed = ci.Fb >= 1 ? (e0 <= tails ? ci.Fb : ci.Fb - 1) : 0;
+            ci.slot_base = ad.slot_base + (ci.o + e0) / B;
+            a.child[(uint64_t)sp * k + b] = ci;
+            const Sub c{ci.o, ci.m, S.arr, S.level + 1, ci.eps, 0};
+            route_sub(c, a.plan, small_max_m, a.next_big, a.next_big_count, a.big_cap, a.small, a.small_count,
+                      a.medium, a.medium_count, a.small_cap, a.bigfy, a.bigfy_count, a.bigfy_cap, a.status);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ resolve
+
+__global__ void resolve_kernel(LevelArgs a) {
+    const uint32_t ntiles = a.counters[0];
+    const uint32_t k = a.k, B = a.B;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const TileRef tr = a.tiles[tile];
+        const TileInfo ti = a.tinfo[tile];
+        for (uint32_t h = threadIdx.x; h < ti.home_used; h += blockDim.x) {
+            const uint32_t w = a.words[ti.hs0 + h];
+            const uint32_t b = (w >> kBlkBits) & (kMaxK - 1u);
+            const uint32_t blk = w & ((1u << kBlkBits) - 1u);
+            const ChildInfo ci = a.child[(uint64_t)tr.sp * k + b];
+            const uint32_t J = a.FBc[(uint64_t)tile * k + b] + blk;
+            uint32_t nw;
+            if (J < ci.placed) {
+                const uint64_t d = ci.slot_base + J;
+                if (d > kWordDestMask) report(a.status, RIP_EINVAL, 0x6301, d);
+                nw = kWordOcc | (uint32_t)d;
+            } else {
+                const uint64_t off = atomicAdd((unsigned long long*)a.pool_used, (unsigned long long)B);
+                if (off + B > a.pool_cap) report(a.status, RIP_EWORKSPACE, 0x6302, off);
+                const uint32_t rec = atomicAdd(&a.counters[2], 1u);
+                if (rec < a.dem_cap)
+                    a.dem[rec] = DemRec{tr.sp, tile, b, blk, off};
+                else
+                    report(a.status, RIP_EWORKSPACE, 0x6303, rec);
+                nw = kWordOcc | kWordDem | rec;
+            }
+            a.words[ti.hs0 + h] = nw;
+        }
+    }
+}
+
+__global__ void prefix_kernel(LevelArgs a) {
+    __shared__ uint64_t scan64[32];
+    __shared__ uint64_t carry;
+    const uint32_t ntiles = a.counters[0];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < ntiles; c0 += blockDim.x) {
+        const uint32_t t = c0 + threadIdx.x;
+        const uint64_t v = t < ntiles ? a.tinfo[t].home_used : 0;
+        uint64_t total;
+        const uint64_t ex = block_exclusive_scan<uint64_t>(v, scan64, &total);
+        if (t < ntiles) a.cand_prefix[t] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        a.cand_prefix[ntiles] = carry;
+        a.counters[4] = 0;  // candidate cursor (64-bit, words 4..5)
+        a.counters[5] = 0;
+    }
+}
+
+// ------------------------------------------------------------------ permute
+
+template <typename U>
+__global__ void __launch_bounds__(kPermuteThreads) permute_kernel(LevelArgs a, uint32_t w) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t units = a.B * w / (uint32_t)sizeof(U);
+    const uint32_t tid = threadIdx.x;
+    const uint32_t g = tid / kGroup, lg = tid % kGroup;
+    const uint32_t gmask = 0xFFu << ((tid & 31u) & ~(kGroup - 1u));
+    const uint32_t leader_lane = (tid & 31u) & ~(kGroup - 1u);
+    const bool leader = lg == 0;
+    U* buf = reinterpret_cast<U*>(smem_raw) + (size_t)g * units;
+    const uint32_t ntiles = a.counters[0];
+    const uint64_t total = a.cand_prefix[ntiles];
+    const uint64_t slot_bytes = (uint64_t)a.B * w;
+
+    bool carrying = false;
+    uint32_t dw = 0;
+    char* abase = nullptr;
+    uint64_t aslot = 0, anslots = 0;
+    uint64_t c = 0, cend = 0;
+    uint32_t spins = 0;
+
+    for (;;) {
+        if (!carrying) {
+            if (c >= cend) {
+                uint64_t c0 = 0;
+                if (leader) c0 = atomicAdd((unsigned long long*)&a.counters[4], 32ull);
+                c0 = __shfl_sync(gmask, c0, leader_lane);
+                if (c0 >= total) break;
+                c = c0;
+                cend = min(c0 + 32, total);
+            }
+            uint32_t ok = 0, w0 = 0;
+            uint64_t s = 0;
+            if (leader) {
+                // tile of candidate c: last t with cand_prefix[t] <= c
+                uint32_t lo = 0, hi = ntiles;
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (a.cand_prefix[mid] <= c) lo = mid; else hi = mid;
+                }
+                const TileInfo ti = a.tinfo[lo];
+                s = ti.hs0 + (c - a.cand_prefix[lo]);
+                const ArrayDesc ad = a.arrays[a.big[a.tiles[lo].sp].arr];
+                abase = ad.data;
+                aslot = ad.slot_base;
+                anslots = ad.n / a.B;  // whole slots of the array
+                w0 = ld_relaxed(&a.words[s]);
+                if ((w0 >> 30) == 1u) ok = atomicCAS(&a.words[s], w0, w0 | kWordTaken) == w0;
+            }
+            ++c;
+            ok = __shfl_sync(gmask, ok, leader_lane);
+            if (!ok) continue;
+            w0 = __shfl_sync(gmask, w0, leader_lane);
+            s = __shfl_sync(gmask, s, leader_lane);
+            abase = reinterpret_cast<char*>(__shfl_sync(gmask, reinterpret_cast<uint64_t>(abase), leader_lane));
+            aslot = __shfl_sync(gmask, aslot, leader_lane);
+            anslots = __shfl_sync(gmask, anslots, leader_lane);
+            if (s < aslot || s - aslot >= anslots) {
+                if (leader) report(a.status, RIP_EINTERNAL, 0x6403, s);
+                continue;
+            }
+            const U* sp = reinterpret_cast<const U*>(abase + (s - aslot) * slot_bytes);
+            for (uint32_t u = lg; u < units; u += kGroup) buf[u] = ld_cg(sp + u);
+            __syncwarp(gmask);
+            if (leader) {
+                __threadfence();
+                st_release(&a.words[s], 0u);
+            }
+            carrying = true;
+            dw = w0;
+            continue;
+        }
+
+        if (dw & kWordDem) {
+            if ((dw & kWordDestMask) >= min(a.counters[2], a.dem_cap)) {
+                if (leader) report(a.status, RIP_EINTERNAL, 0x6404, dw);
+                carrying = false;
+                continue;
+            }
+            const DemRec rec = a.dem[dw & kWordDestMask];
+            if (rec.pool_off + a.B > a.pool_cap) {
+                if (leader) report(a.status, RIP_EINTERNAL, 0x6405, rec.pool_off);
+                carrying = false;
+                continue;
+            }
+            U* dst = reinterpret_cast<U*>(a.pool + rec.pool_off * w);
+            for (uint32_t u = lg; u < units; u += kGroup) dst[u] = buf[u];
+            __syncwarp(gmask);
+            carrying = false;
+            continue;
+        }
+        const uint64_t d = dw & kWordDestMask;
+        if (d < aslot || d - aslot >= anslots) {  // never write outside the array
+            if (leader) report(a.status, RIP_EINTERNAL, 0x6402, d);
+            carrying = false;
+            continue;
+        }
+        U* dp = reinterpret_cast<U*>(abase + (d - aslot) * slot_bytes);
+        U y[4];
+#pragma unroll
+        for (uint32_t j = 0; j < 4; ++j) {
+            const uint32_t u = lg + j * kGroup;
+            if (u < units) y[j] = ld_cg(dp + u);
+        }
+        uint32_t old = 0;
+        if (leader) old = atom_or_acqrel(&a.words[d], kWordTaken);
+        old = __shfl_sync(gmask, old, leader_lane);
+        if (old & kWordTaken) {
+            // a chain start holds the slot: wait until it has read it out
+            if (leader) {
+                while (ld_acquire(&a.words[d]) != 0u) {
+                    if (++spins > (1u << 24)) {
+                        report(a.status, RIP_ETIMEOUT, 0x6401, d);
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            spins = __shfl_sync(gmask, spins, leader_lane);
+            if (spins > (1u << 24)) {
+                carrying = false;  // give up; the error is reported
+                continue;
+            }
+            __syncwarp(gmask);
+            continue;
+        }
+        if (old & kWordOcc) {
+            // swap: read the block at d, write ours, carry the one read
+#pragma unroll
+            for (uint32_t j = 0; j < 4; ++j) {
+                const uint32_t u = lg + j * kGroup;
+                if (u < units) {
+                    dp[u] = buf[u];
+                    buf[u] = y[j];
+                }
+            }
+            for (uint32_t u = lg + 4 * kGroup; u < units; u += kGroup) {
+                const U t = ld_cg(dp + u);
+                dp[u] = buf[u];
+                buf[u] = t;
+            }
+            __syncwarp(gmask);
+            dw = old;
+        } else {
+            for (uint32_t u = lg; u < units; u += kGroup) dp[u] = buf[u];
+            __syncwarp(gmask);
+            carrying = false;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ tails
+
+template <int W>
+__global__ void tails_kernel(LevelArgs a) {
+    using T = typename Elem<W>::T;
+    __shared__ uint32_t pre[kMaxK];
+    __shared__ uint32_t scan[32];
+    const uint32_t ntiles = a.counters[0];
+    const uint32_t k = a.k, B = a.B;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const T* pool = reinterpret_cast<const T*>(a.pool);
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const TileRef tr = a.tiles[tile];
+        const TileInfo ti = a.tinfo[tile];
+        const Sub S = a.big[tr.sp];
+        T* base = reinterpret_cast<T*>(a.arrays[S.arr].data);
+        const uint32_t i0 = 2 * threadIdx.x, i1 = 2 * threadIdx.x + 1;
+        const uint32_t r0 = i0 < k ? a.C[(uint64_t)tile * k + i0] % B : 0;
+        const uint32_t r1 = i1 < k ? a.C[(uint64_t)tile * k + i1] % B : 0;
+        const uint32_t ex = block_exclusive_scan<uint32_t>(r0 + r1, scan, nullptr);
+        if (i0 < k) pre[i0] = ex;
+        if (i1 < k) pre[i1] = ex + r0;
+        __syncthreads();
+        for (uint32_t b = warp; b < k; b += nwarps) {
+            const uint64_t ci_idx = (uint64_t)tile * k + b;
+            const uint32_t R = a.C[ci_idx] % B;
+            if (R == 0) continue;
+            const ChildInfo ci = a.child[(uint64_t)tr.sp * k + b];
+            const uint64_t x0 = (uint64_t)B * ci.Fb + a.TLc[ci_idx];
+            const T* src = pool + ti.pool_base + pre[b];
+            const uint64_t n_arr = a.arrays[S.arr].n;
+            if (ti.pool_base + pre[b] + R > a.pool_cap || x0 + R > ci.m || ci.o + ci.m > n_arr) {
+                if (lane == 0) report(a.status, RIP_EINTERNAL, 0x6601, x0);
+                continue;
+            }
+            for (uint32_t j = lane; j < R; j += 32u) {
+                uint64_t xe = x0 + j + ci.eps;
+                if (xe >= ci.m) xe -= ci.m;
+                base[ci.o + xe] = src[j];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int W>
+__global__ void demoted_kernel(LevelArgs a) {
+    using T = typename Elem<W>::T;
+    const uint32_t ndem = min(a.counters[2], a.dem_cap);
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    const T* pool = reinterpret_cast<const T*>(a.pool);
+    for (uint32_t i = gw; i < ndem; i += nw) {
+        const DemRec rec = a.dem[i];
+        const ChildInfo ci = a.child[(uint64_t)rec.sp * a.k + rec.b];
+        const uint64_t J = (uint64_t)a.FBc[(uint64_t)rec.tile * a.k + rec.b] + rec.blk;
+        const ArrayDesc ad = a.arrays[a.big[rec.sp].arr];
+        T* base = reinterpret_cast<T*>(ad.data);
+        if ((J + 1) * a.B > ci.m || ci.o + ci.m > ad.n || rec.pool_off + a.B > a.pool_cap) {
+            if (lane == 0) report(a.status, RIP_EINTERNAL, 0x6701, J);
+            continue;
+        }
+        for (uint32_t j = lane; j < a.B; j += 32u) {
+            uint64_t xe = J * a.B + j + ci.eps;
+            if (xe >= ci.m) xe -= ci.m;
+            base[ci.o + xe] = pool[rec.pool_off + j];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ large leaves
+
+// Leaves too large for one SM (only with plans whose base or level cap
+// exceeds the on-SM limit): undo the rotation in place, then a plain
+// sequential Fisher-Yates in global memory, one thread per leaf.
+template <int W>
+__global__ void bigfy_kernel(const Sub* list, const uint32_t* count, uint32_t cap, const ArrayDesc* arrays,
+                             DevPlan plan, const uint32_t* leftover, Status* status) {
+    using T = typename Elem<W>::T;
+    const uint32_t n = min(*count, cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && *leftover != 0)  // deeper recursion than the host planned
+        report(status, RIP_EWORKSPACE, 0x6501, *leftover);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const Sub s = list[i];
+        const ArrayDesc ad = arrays[s.arr];
+        T* x = reinterpret_cast<T*>(ad.data) + s.o;
+        const uint64_t m = s.m;
+        if (m > (1ull << 32)) {  // Fisher-Yates draws are 32-bit (Lemire with 32-bit words)
+            report(status, RIP_EINVAL, 0x6502, m);
+            continue;
+        }
+        auto rev = [&](uint64_t l, uint64_t r) {  // reverse x[l..r)
+            while (l + 1 < r) {
+                --r;
+                const T t = x[l];
+                x[l] = x[r];
+                x[r] = t;
+                ++l;
+            }
+        };
+        if (s.eps) {  // physical = rotate-left of logical by (m - eps): three reversals
+            const uint64_t e = s.eps;
+            rev(0, e);
+            rev(e, m);
+            rev(0, m);
+            // now logical i sits at physical i
+        }
+        FyStream fs;
+        fs.init(make_key(ad.seed), s.level, s.o);
+        for (uint64_t j = m - 1; j >= 1; --j) {
+            const uint64_t p = fs.draw(j);
+            const T t = x[j];
+            x[j] = x[p];
+            x[p] = t;
+        }
+    }
+}
+
+}  // namespace
+
+size_t classify_smem_bytes(uint32_t k, uint32_t B, uint32_t w) {
+    return ((sizeof(ClsShared) + 15) & ~size_t(15)) + (size_t)k * B * w;
+}
+
+size_t permute_smem_bytes(uint32_t B, uint32_t w) {
+    return (size_t)(kPermuteThreads / kGroup) * B * w;
+}
+
+cudaError_t launch_init(const InitArgs& a, cudaStream_t s) {
+    init_kernel<<<1, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int W>
+static cudaError_t launch_level_w(const LevelArgs& a, uint32_t num_sms, cudaStream_t s, uint32_t* launches) {
+    constexpr int E = W == 16 ? 4 : 8;
+    cudaError_t err;
+    tiles_kernel<<<1, 1024, 0, s>>>(a);
+    const size_t csm = classify_smem_bytes(a.k, a.B, W);
+    err = cudaFuncSetAttribute(classify_kernel<W, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+    if (err != cudaSuccess) return err;
+    classify_kernel<W, E><<<num_sms, kClassifyThreads, csm, s>>>(a);
+    scan_kernel<<<num_sms * 2, 512, 0, s>>>(a, a.small_max_m);
+    resolve_kernel<<<num_sms * 4, 256, 0, s>>>(a);
+    prefix_kernel<<<1, 1024, 0, s>>>(a);
+    const size_t psm = permute_smem_bytes(a.B, W);
+    if (a.vec16) {
+        err = cudaFuncSetAttribute(permute_kernel<uint4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
+        if (err != cudaSuccess) return err;
+        permute_kernel<uint4><<<num_sms * 8, kPermuteThreads, psm, s>>>(a, W);
+    } else {
+        using T = typename Elem<W>::T;
+        err = cudaFuncSetAttribute(permute_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
+        if (err != cudaSuccess) return err;
+        permute_kernel<T><<<num_sms * 8, kPermuteThreads, psm, s>>>(a, W);
+    }
+    tails_kernel<W><<<num_sms * 4, 512, 0, s>>>(a);
+    demoted_kernel<W><<<num_sms, 256, 0, s>>>(a);
+    if (launches) *launches += 8;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_level(const LevelArgs& a, uint32_t w, uint32_t num_sms, cudaStream_t s, uint32_t* launches) {
+    switch (w) {
+        case 4: return launch_level_w<4>(a, num_sms, s, launches);
+        case 8: return launch_level_w<8>(a, num_sms, s, launches);
+        default: return launch_level_w<16>(a, num_sms, s, launches);
+    }
+}
+
+cudaError_t launch_bigfy(const Sub* list, const uint32_t* count, uint32_t cap, const ArrayDesc* arrays,
+                         DevPlan plan, uint32_t w, const uint32_t* leftover, Status* status, cudaStream_t s) {
+    switch (w) {
+        case 4: bigfy_kernel<4><<<8, 32, 0, s>>>(list, count, cap, arrays, plan, leftover, status); break;
+        case 8: bigfy_kernel<8><<<8, 32, 0, s>>>(list, count, cap, arrays, plan, leftover, status); break;
+        default: bigfy_kernel<16><<<8, 32, 0, s>>>(list, count, cap, arrays, plan, leftover, status); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace rip

@@ -1,0 +1,329 @@
+// rip_small.cu -- finishes whole subproblems that fit on one SM.
+//
+// A subproblem of m <= 48K elements is loaded once (through its rotation),
+// its complete remaining recursion -- scatter levels (Sec. 2.2 ScatterShuffle,
+// Sec. 3.2 recursion) down to Fisher-Yates leaves (Sec. 2.2, Fig. 1) -- runs
+// on 16-bit index arrays in shared memory, and the result is written back in
+// canonical (unrotated) order with one coalesced pass.  HBM traffic: one read
+// and one write of the subproblem, whatever the number of levels inside.
+//
+// Shared memory: [fixed scratch | P0 (2m) | P1 (2m) | D (w*m)].  In "medium"
+// mode D lives in a per-CTA slice of global scratch instead (m up to 48K).
+#include "rip_internal.cuh"
+
+namespace rip {
+
+namespace {
+
+constexpr uint32_t kThreads = kSmallThreads;
+constexpr uint32_t kWarps = kThreads / 32;
+constexpr uint32_t kE = 4;  // 32-element steps per ranking warp per round
+
+struct SmallShared {
+    uint32_t thr[kSmallCntCap];  // per (tile, bucket): count, then B*floor(count/B)
+    uint32_t fb[kSmallCntCap];   // per (tile, bucket): first full-block destination
+    uint32_t tb[kSmallCntCap];   // per (tile, bucket): tail destination minus thr
+    uint32_t run[kMaxK];         // per bucket: elements seen so far in the current tile
+    uint16_t tbl[kSmallTbl];     // per (ranking warp, bucket): running count in a round
+    uint64_t stack[kSmallStack]; // pending scatter ranges
+    uint32_t scan[32];
+    uint32_t stack_top;
+    uint32_t cur_hi, cur_lo;
+    uint32_t flag;
+};
+
+__device__ __forceinline__ uint64_t pack_range(uint32_t a, uint32_t len, uint32_t L, uint32_t buf) {
+    return (uint64_t)a | ((uint64_t)len << 20) | ((uint64_t)L << 40) | ((uint64_t)buf << 48);
+}
+
+// One Fisher-Yates pass over Z[0..len) by the calling thread (Sec. 2.2).
+__device__ void fy_serial(uint16_t* Z, uint32_t len, PhiloxKey key, uint32_t L, uint64_t leaf_o) {
+    FyStream fs;
+    fs.init(key, L, leaf_o);
+    for (uint32_t i = len - 1; i >= 1; --i) {
+        const uint32_t j = (uint32_t)fs.draw(i);
+        const uint16_t zi = Z[i];
+        Z[i] = Z[j];
+        Z[j] = zi;
+    }
+}
+
+// Fisher-Yates over Z[0..len) with the partner draws computed by the whole
+// block into `draws` first; the dependent swap chain then runs on thread 0.
+__device__ void fy_block(uint16_t* Z, uint16_t* draws, uint32_t len, PhiloxKey key, uint32_t L,
+                         uint64_t leaf_o) {
+    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
+        if (i == 0) continue;
+        const uint64_t p = leaf_o + i;
+        const uint64_t q = p >> 2;
+        const uint4 r = philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), L | (kTagFy << 8), (uint32_t)leaf_o, key);
+        uint64_t v;
+        if (!lemire_accept(pick(r, (uint32_t)(p & 3u)), i + 1, v)) v = fy_draw_retry(key, L, leaf_o, p, i + 1);
+        draws[i] = (uint16_t)v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (uint32_t i = len - 1; i >= 1; --i) {
+            const uint32_t j = draws[i];
+            const uint16_t zi = Z[i];
+            Z[i] = Z[j];
+            Z[j] = zi;
+        }
+    }
+    __syncthreads();
+}
+
+// One scatter level of the range [a, a+len) (level L) from X into Y, both
+// index arrays; children ranges are finished (leaves) or pushed.
+__device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint32_t a, uint32_t len,
+                              uint32_t L, uint32_t buf, const DevPlan& plan, PhiloxKey key,
+                              uint64_t sub_o, Status* status) {
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t li = plan.idx(L);
+    const uint32_t k = plan.k[li], B = plan.B[li];
+    const uint64_t T64 = plan.T[li];
+    const uint32_t T = T64 >= len ? len : (uint32_t)T64;
+    const uint32_t tiles = (len + T - 1) / T;
+    const uint32_t ncnt = tiles * k;
+    uint16_t* X = buf ? P1 : P0;
+    uint16_t* Y = buf ? P0 : P1;
+    const uint64_t o_r = sub_o + a;  // logical global start of this range
+
+    if (ncnt > kSmallCntCap || k > kMaxK) {  // excluded by the host's eligibility rule
+        if (tid == 0) report(status, RIP_EINTERNAL, 0x5101, ncnt);
+        return;
+    }
+    for (uint32_t j = tid; j < ncnt; j += blockDim.x) sh.thr[j] = 0;
+    __syncthreads();
+
+    // counts per (tile, bucket)
+    for (uint32_t ib = warp * 32u; ib < len; ib += kWarps * 32u) {
+        const uint32_t i = ib + lane;
+        const uint32_t word = warp_scatter_word(key, L, o_r, o_r + ib);
+        const bool valid = i < len;
+        const uint32_t key2 = valid ? (i / T) * k + bucket_of(word, k) : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, key2);
+        if (valid && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&sh.thr[key2], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+
+    // bucket sizes -> region starts s_b (exclusive scan over b)
+    for (uint32_t b = tid; b < k; b += blockDim.x) {
+        uint32_t size = 0;
+        for (uint32_t t = 0; t < tiles; ++t) size += sh.thr[t * k + b];
+        sh.run[b] = size;
+    }
+    __syncthreads();
+    {
+        // k <= kMaxK = 1024 = 2 * kThreads: two entries per thread
+        const uint32_t i0 = 2 * tid, i1 = 2 * tid + 1;
+        const uint32_t v0 = i0 < k ? sh.run[i0] : 0, v1 = i1 < k ? sh.run[i1] : 0;
+        const uint32_t ex = block_exclusive_scan<uint32_t>(v0 + v1, sh.scan, nullptr);
+        if (i0 < k) sh.run[i0] = ex;
+        if (i1 < k) sh.run[i1] = ex + v0;
+    }
+    __syncthreads();
+    // per (tile, bucket): full-block and tail destinations of the canonical layout
+    for (uint32_t b = tid; b < k; b += blockDim.x) {
+        const uint32_t sb = sh.run[b];
+        uint32_t Fb = 0;
+        for (uint32_t t = 0; t < tiles; ++t) Fb += sh.thr[t * k + b] / B;
+        uint32_t fsum = 0, rsum = 0;
+        for (uint32_t t = 0; t < tiles; ++t) {
+            const uint32_t c = sh.thr[t * k + b];
+            const uint32_t th = c - c % B;
+            sh.fb[t * k + b] = sb + B * fsum;
+            sh.tb[t * k + b] = sb + B * Fb + rsum - th;
+            sh.thr[t * k + b] = th;
+            fsum += c / B;
+            rsum += c % B;
+        }
+    }
+    __syncthreads();
+
+    // stable ranks inside each (tile, bucket), then the move X -> Y
+    const uint32_t nwr = min(kWarps, (uint32_t)kSmallTbl / k);
+    const uint32_t round = nwr * 32u * kE;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    for (uint32_t t = 0; t < tiles; ++t) {
+        const uint32_t lo = t * T, hi = min(lo + T, len);
+        for (uint32_t b = tid; b < k; b += blockDim.x) sh.run[b] = 0;
+        for (uint32_t j = tid; j < nwr * k; j += blockDim.x) sh.tbl[j] = 0;
+        __syncthreads();
+        for (uint32_t R = lo; R < hi; R += round) {
+            uint32_t bb[kE], pr[kE];
+            if (warp < nwr) {
+#pragma unroll
+                for (uint32_t e = 0; e < kE; ++e) {
+                    const uint32_t ib = R + (warp * kE + e) * 32u;
+                    const uint32_t i = ib + lane;
+                    const bool valid = i < hi;
+                    const uint32_t word = warp_scatter_word(key, L, o_r, o_r + ib);
+                    const uint32_t b = bucket_of(word, k);
+                    const uint32_t kk = valid ? b : 0xffffffffu;
+                    const uint32_t peers = __match_any_sync(0xffffffffu, kk);
+                    const uint32_t pre = valid ? sh.tbl[warp * k + b] : 0u;
+                    __syncwarp();
+                    if (valid && lane == (uint32_t)(__ffs(peers) - 1))
+                        sh.tbl[warp * k + b] = (uint16_t)(pre + __popc(peers));
+                    __syncwarp();
+                    bb[e] = valid ? b : 0xffffffffu;
+                    pr[e] = pre + __popc(peers & lt_mask);
+                }
+            }
+            __syncthreads();
+            if (warp < nwr) {
+#pragma unroll
+                for (uint32_t e = 0; e < kE; ++e) {
+                    const uint32_t b = bb[e];
+                    if (b == 0xffffffffu) continue;
+                    uint32_t cross = 0;
+                    for (uint32_t w = 0; w < warp; ++w) cross += sh.tbl[w * k + b];
+                    const uint32_t rank = sh.run[b] + cross + pr[e];
+                    const uint32_t ci = t * k + b;
+                    const uint32_t d = rank < sh.thr[ci] ? sh.fb[ci] + rank : sh.tb[ci] + rank;
+                    const uint32_t i = R + (warp * kE + e) * 32u + lane;
+                    if (d >= len) {  // cannot happen for consistent counts; never write out of range
+                        report(status, RIP_EINTERNAL, 0x5103, d);
+                        continue;
+                    }
+                    Y[a + d] = X[a + i];
+                }
+            }
+            __syncthreads();
+            for (uint32_t b = tid; b < k; b += blockDim.x) {
+                uint32_t tot = 0;
+                for (uint32_t w = 0; w < nwr; ++w) {
+                    tot += sh.tbl[w * k + b];
+                    sh.tbl[w * k + b] = 0;
+                }
+                sh.run[b] += tot;
+            }
+            __syncthreads();
+        }
+    }
+
+    // children: leaves now, larger ones onto the stack
+    for (uint32_t b = tid; b < k; b += blockDim.x) {
+        const uint32_t sb = sh.fb[b];  // tile 0 entry = s_b
+        const uint32_t se = b + 1 < k ? sh.fb[b + 1] : len;
+        const uint32_t size = se - sb;
+        if (size == 0) continue;
+        if (se > len || sb > se) {
+            report(status, RIP_EINTERNAL, 0x5104, se);
+            continue;
+        }
+        if (size == 1 || plan.is_leaf(size, L + 1)) {
+            uint16_t* Z = Y + a + sb;
+            if (size > 1) fy_serial(Z, size, key, L + 1, o_r + sb);
+            if (Y != P0)
+                for (uint32_t j = 0; j < size; ++j) P0[a + sb + j] = Z[j];
+        } else {
+            const uint32_t slot = atomicAdd(&sh.stack_top, 1u);
+            if (slot < kSmallStack)
+                sh.stack[slot] = pack_range(a + sb, size, L + 1, buf ^ 1u);
+            else
+                report(status, RIP_EINTERNAL, 0x5102, slot);
+        }
+    }
+    __syncthreads();
+}
+
+template <int W>
+__global__ void __launch_bounds__(kThreads, 1) small_kernel(SmallArgs args) {
+    using T = typename Elem<W>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmallShared& sh = *reinterpret_cast<SmallShared*>(smem_raw);
+    unsigned char* dyn = smem_raw + ((sizeof(SmallShared) + 15) & ~size_t(15));
+    const uint32_t count = min(*args.count, args.capacity);
+    const uint32_t tid = threadIdx.x;
+    const DevPlan& plan = args.plan;
+
+    for (uint32_t item = blockIdx.x; item < count; item += gridDim.x) {
+        const Sub s = args.list[item];
+        const ArrayDesc ad = args.arrays[s.arr];
+        T* base = reinterpret_cast<T*>(ad.data);
+        const uint32_t m = (uint32_t)s.m;
+        const PhiloxKey key = make_key(ad.seed);
+        uint16_t* P0 = reinterpret_cast<uint16_t*>(dyn);
+        uint16_t* P1 = P0 + ((m + 7u) & ~7u);
+        T* D = args.medium ? reinterpret_cast<T*>(args.gscratch + (uint64_t)blockIdx.x * args.gslot_bytes)
+                           : reinterpret_cast<T*>(P1 + ((m + 7u) & ~7u));
+
+        for (uint32_t i = tid; i < m; i += blockDim.x) {
+            D[i] = base[phys_index(s, i)];
+            P0[i] = (uint16_t)i;
+        }
+        if (tid == 0) sh.stack_top = 0;
+        __syncthreads();
+
+        if (plan.is_leaf(m, s.level)) {
+            if (m > 1) fy_block(P0, P1, m, key, s.level, s.o);
+        } else {
+            if (tid == 0) {
+                sh.stack[0] = pack_range(0, m, s.level, 0);
+                sh.stack_top = 1;
+            }
+            for (;;) {
+                __syncthreads();
+                if (tid == 0) {
+                    const uint32_t top = min(sh.stack_top, (uint32_t)kSmallStack);
+                    if (top == 0) {
+                        sh.flag = 1;
+                    } else {
+                        const uint64_t e = sh.stack[top - 1];
+                        sh.stack_top = top - 1;
+                        sh.cur_lo = (uint32_t)e;
+                        sh.cur_hi = (uint32_t)(e >> 32);
+                        sh.flag = 0;
+                    }
+                }
+                __syncthreads();
+                if (sh.flag) break;
+                const uint64_t e = ((uint64_t)sh.cur_hi << 32) | sh.cur_lo;
+                const uint32_t a = (uint32_t)(e & 0xFFFFFu);
+                const uint32_t len = (uint32_t)((e >> 20) & 0xFFFFFu);
+                const uint32_t L = (uint32_t)((e >> 40) & 0xFFu);
+                const uint32_t buf = (uint32_t)((e >> 48) & 1u);
+                __syncthreads();
+                scatter_range(sh, P0, P1, a, len, L, buf, plan, key, s.o, args.status);
+            }
+        }
+        __syncthreads();
+        for (uint32_t i = tid; i < m; i += blockDim.x) base[s.o + i] = D[P0[i]];
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+size_t small_fixed_smem() { return (sizeof(SmallShared) + 15) & ~size_t(15); }
+
+size_t small_smem_bytes(uint64_t m, uint32_t w, bool medium) {
+    const uint64_t mr = (m + 7u) & ~7ull;
+    return small_fixed_smem() + 4 * mr + (medium ? 0 : w * mr);
+}
+
+cudaError_t launch_small(const SmallArgs& args, uint32_t w, size_t smem, uint32_t grid, cudaStream_t stream) {
+    cudaError_t err;
+    switch (w) {
+        case 4:
+            err = cudaFuncSetAttribute(small_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (err != cudaSuccess) return err;
+            small_kernel<4><<<grid, kThreads, smem, stream>>>(args);
+            break;
+        case 8:
+            err = cudaFuncSetAttribute(small_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (err != cudaSuccess) return err;
+            small_kernel<8><<<grid, kThreads, smem, stream>>>(args);
+            break;
+        default:
+            err = cudaFuncSetAttribute(small_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (err != cudaSuccess) return err;
+            small_kernel<16><<<grid, kThreads, smem, stream>>>(args);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace rip

@@ -1,0 +1,83 @@
+"""The C-ABI library builds, loads and exports every entry point the header
+declares; host-side argument checks work without a GPU (no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2302_03317_gb300 as rip
+from paper_2302_03317_gb300 import build as libbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER_DIR = os.path.join(ROOT, "include")
+
+
+def _declared_functions():
+    names = []
+    for fn in sorted(os.listdir(HEADER_DIR)):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(HEADER_DIR, fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(rip_\w+)\s*\(", text, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_library_builds_for_sm103a():
+    path = libbuild.build()
+    assert os.path.exists(path)
+    assert "-gencode=arch=compute_103a,code=sm_103a" in libbuild.FLAGS
+
+
+def test_every_declared_symbol_is_exported():
+    names = _declared_functions()
+    assert len(names) >= 10, names
+    lib = ctypes.CDLL(libbuild.build())
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+
+
+def test_strerror_and_invalid_arguments():
+    assert rip.rip_strerror(rip.RIP_OK) == "ok"
+    assert "invalid" in rip.rip_strerror(rip.RIP_EINVAL)
+    lib = rip._load()
+    # bad element width: rejected on the host before any CUDA call
+    assert lib.rip_shuffle(None, 10, 3, 1, None) == rip.RIP_EINVAL
+    assert lib.rip_shuffle_ex(None, 10, 12, 1, None, None, 0, None) == rip.RIP_EINVAL
+    # NULL data with n > 1
+    assert lib.rip_shuffle(None, 10, 4, 1, None) == rip.RIP_EINVAL
+    # misaligned pointer for 8-byte elements
+    assert lib.rip_shuffle(ctypes.c_void_p(4), 10, 8, 1, None) == rip.RIP_EINVAL
+    assert lib.rip_last_call_info(None) == rip.RIP_EINVAL
+    assert lib.rip_digest(None, 10, 4, None, None) == rip.RIP_EINVAL
+
+
+def test_default_plan_and_workspace_size_on_host():
+    p = rip.rip_default_plan(1 << 30, 8)
+    assert p.ks[0] == 256 and p.base == 4096
+    assert p.ks[0] * p.Bs[0] * 8 == 128 * 1024
+    assert p.Ts[0] % p.Bs[0] == 0
+    small = rip.rip_default_plan(1 << 20, 4)
+    assert small.ks[0] == 64  # below 128 MiB of data (Sec. 5)
+    ws = rip.rip_shuffle_workspace_size(1 << 30, 8)
+    assert 0 < ws < (1 << 30) * 8 * 0.03  # a few percent of the input at most
+    bad = rip.Plan(ks=[3], Ts=[8], Bs=[2], base=4)
+    assert rip.rip_shuffle_workspace_size(100, 4, bad) == 0
+    nested_bad = rip.Plan(ks=[4, 4], Ts=[16, 16], Bs=[2, 4], base=4)  # B must divide the previous B
+    assert rip.rip_shuffle_workspace_size(100, 4, nested_bad) == 0
+
+
+def test_oracle_and_library_share_no_code():
+    """The oracle (test infrastructure) and the CUDA sources include nothing of each other."""
+    csrc = os.path.join(ROOT, "paper_2302_03317_gb300", "csrc")
+    for fn in os.listdir(csrc):
+        text = open(os.path.join(csrc, fn)).read()
+        includes = re.findall(r"^\s*#\s*include\s*[<\"]([^>\"]+)", text, flags=re.M)
+        assert not any("oracle" in inc for inc in includes), fn
+    pkg = open(os.path.join(ROOT, "paper_2302_03317_gb300", "__init__.py")).read()
+    assert "import oracle" not in pkg and "from oracle" not in pkg
+    orc = open(os.path.join(ROOT, "oracle", "rip_oracle.c")).read()
+    assert "#include \"" not in orc

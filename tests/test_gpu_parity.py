@@ -1,0 +1,156 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle,
+element by element, on seeded synthetic inputs (iota, records)."""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_2302_03317_gb300 as rip  # noqa: E402
+
+
+def _np_dtype(w):
+    return {4: np.uint32, 8: np.uint64}[w]
+
+
+def _make(n, w):
+    """iota for 4/8-byte elements; 16-byte records {key = i, payload = splitmix64(i)}."""
+    if w in (4, 8):
+        return np.arange(n, dtype=_np_dtype(w))
+    from paper_2302_03317_gb300.inputs import records_np
+    return records_np(n)
+
+
+def _to_dev(a):
+    t = torch.from_numpy(a.view(np.int64) if a.dtype == np.uint64 else
+                         a.view(np.int32) if a.dtype == np.uint32 else a)
+    return t.cuda()
+
+
+def _from_dev(t, like):
+    return t.cpu().numpy().view(like.dtype).reshape(like.shape)
+
+
+def _oplan(p: rip.Plan):
+    return oracle.Plan(list(p.ks), list(p.Ts), list(p.Bs), p.base, p.max_levels)
+
+
+def check(n, w, plan, seed, offset=0):
+    a = _make(n + offset, w)
+    t = _to_dev(a)
+    view = t[offset:]
+    rip.shuffle_(view, seed, plan=plan, check=True)
+    got = _from_dev(view, a[offset:])
+    want = oracle.shuffle(np.ascontiguousarray(a[offset:]), seed, _oplan(plan))
+    if not np.array_equal(got, want):
+        diff = np.flatnonzero((got != want).reshape(n, -1).any(axis=1))
+        pytest.fail(f"n={n} w={w} seed={seed}: {diff.size} mismatches, first at {diff[:8]}")
+    if offset:
+        assert np.array_equal(_from_dev(t[:offset], a[:offset]), a[:offset])
+
+
+# plans: FY only, scatter inside one SM, nested levels inside one SM, in place with one and
+# two levels, tiny in-place parameters (deep recursion, many demotions), records
+FY = rip.Plan(ks=[2], Ts=[4], Bs=[1], base=1 << 20)
+SMEM1 = rip.Plan(ks=[16], Ts=[512], Bs=[4], base=64)
+SMEM_DEEP = rip.Plan(ks=[4], Ts=[1 << 20], Bs=[8], base=16)
+INPLACE1 = rip.Plan(ks=[64], Ts=[4096], Bs=[256], base=4096)
+INPLACE2 = rip.Plan(ks=[16], Ts=[65536], Bs=[64], base=4096)
+TINY = rip.Plan(ks=[2], Ts=[8], Bs=[2], base=3)
+MIXED = rip.Plan(ks=[8, 4], Ts=[3000, 1 << 20], Bs=[6, 3], base=50)
+CFG1 = rip.Plan(ks=[64], Ts=[4096], Bs=[256], base=4096, max_levels=1)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 17, 1000, 4096, 20000])
+@pytest.mark.parametrize("w", [4, 8, 16])
+def test_fisher_yates_only(n, w):
+    check(n, w, FY, seed=5)
+
+
+@pytest.mark.parametrize("n,w", [(5000, 4), (5000, 8), (3000, 16), (17000, 8), (25000, 4)])
+def test_scatter_inside_one_sm(n, w):
+    check(n, w, SMEM1, seed=2)
+    check(n, w, SMEM_DEEP, seed=3)
+
+
+@pytest.mark.parametrize("n,w", [(1 << 17, 4), (100_003, 8)])
+def test_one_level_in_place(n, w):
+    check(n, w, INPLACE1, seed=1)
+
+
+def test_one_level_in_place_records():
+    check(60_000, 16, rip.Plan(ks=[32], Ts=[4096], Bs=[128], base=4096), seed=1)
+
+
+@pytest.mark.parametrize("n,w", [(1 << 21, 8), (1_500_001, 4)])
+def test_two_levels_in_place(n, w):
+    check(n, w, INPLACE2, seed=7)
+
+
+@pytest.mark.parametrize("n,w", [(100_000, 4), (70_001, 16)])
+def test_tiny_parameters_deep_recursion(n, w):
+    check(n, w, TINY, seed=11)
+
+
+def test_mixed_level_parameters():
+    check(400_000, 4, MIXED, seed=13)
+
+
+def test_config1_exact():
+    """n = 2^20 u32 iota, seed 1, k = 64, T = 4096, B = 256, base 4096, one level then FY."""
+    check(1 << 20, 4, CFG1, seed=1)
+
+
+@pytest.mark.parametrize("n,w", [(1 << 22, 8), (1 << 21, 4), (1 << 20, 16)])
+def test_default_plan(n, w):
+    plan = rip.rip_default_plan(n, w)
+    check(n, w, plan, seed=3)
+
+
+def test_unaligned_start_uses_element_copies():
+    check(200_000, 4, INPLACE1, seed=9, offset=1)
+
+
+def test_deterministic_and_seeded():
+    n = 300_000
+    outs = []
+    for seed in (4, 4, 5):
+        t = torch.arange(n, dtype=torch.int64, device="cuda")
+        rip.shuffle_(t, seed, plan=INPLACE1, check=True)
+        outs.append(t.cpu())
+    assert torch.equal(outs[0], outs[1])
+    assert not torch.equal(outs[0], outs[2])
+
+
+def test_batched_matches_single_calls():
+    sizes = [0, 1, 5, 300, 4096, 5000, 70_000, 200_000]
+    plan = INPLACE1
+    arrays = [np.arange(n, dtype=np.uint32) for n in sizes]
+    ts = [_to_dev(a) for a in arrays]
+    rip.shuffle_batched_(ts, 40, plan=plan, check=True)
+    want = oracle.shuffle_batched(arrays, 40, _oplan(plan))
+    for t, a, wnt in zip(ts, arrays, want):
+        assert np.array_equal(_from_dev(t, a), wnt)
+
+
+def test_digest_matches_oracle():
+    for w, n in [(4, 12345), (8, 1 << 20), (16, 4097)]:
+        a = _make(n, w)
+        t = _to_dev(a)
+        assert rip.digest(t) == oracle.digest(a)
+
+
+def test_caller_workspace_allocates_nothing_else():
+    n = 1 << 20
+    plan = INPLACE1
+    need = rip.rip_shuffle_workspace_size(n, 4, plan)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    a = np.arange(n, dtype=np.uint32)
+    t = _to_dev(a)
+    rip.shuffle_(t, 21, plan=plan, ws=ws, check=True)
+    assert np.array_equal(_from_dev(t, a), oracle.shuffle(a, 21, _oplan(plan)))
+    small = torch.empty(max(need // 2, 256), dtype=torch.uint8, device="cuda")
+    with pytest.raises(rip.RipError):
+        rip.shuffle_(t, 21, plan=plan, ws=small)
