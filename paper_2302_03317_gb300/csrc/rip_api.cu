@@ -160,11 +160,11 @@ Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& 
         prodk = std::min<uint64_t>(prodk * k, (uint64_t)1 << 62);
     }
     L.levels = (uint32_t)caps.size();
+    uint32_t kmax = 2;
+    for (uint32_t l = 0; l < p.num_levels; ++l) kmax = std::max(kmax, p.level[l].k);
     for (const LevelCaps& c : caps) {
         L.big_cap = std::max(L.big_cap, c.big);
         L.tile_cap = (uint32_t)std::max<uint64_t>(L.tile_cap, c.tiles);
-        L.pair_cap = std::max(L.pair_cap, c.pairs);
-        L.child_cap = std::max(L.child_cap, c.children);
         L.pool_cap = std::max(L.pool_cap, c.pool);
         L.dem_cap = (uint32_t)std::max<uint64_t>(L.dem_cap, c.dem);
     }
@@ -173,6 +173,9 @@ Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& 
     L.bigfy_cap = (uint32_t)std::min<uint64_t>(std::min<uint64_t>(bigfy_total, nsum / 2 + 16) + 16, 0x7fffffffull);
     if (L.big_cap == 0) L.big_cap = 1;
     if (L.tile_cap == 0) L.tile_cap = 1;
+    // any level may index (tile, bucket) and (subproblem, bucket) tables with the largest k
+    L.pair_cap = (uint64_t)L.tile_cap * kmax;
+    L.child_cap = (uint64_t)L.big_cap * kmax;
 
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -321,9 +324,14 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
         aligned16 &= (reinterpret_cast<uintptr_t>(ptrs[i]) % 16) == 0;
     }
     ArrayDesc* d_arr = reinterpret_cast<ArrayDesc*>(wsp + lay.arrays);
-    if (cudaMemcpyAsync(d_arr, arr.data(), sizeof(ArrayDesc) * arr.size(), cudaMemcpyHostToDevice, stream) !=
-        cudaSuccess)
+    InitArgs ia{};
+    if (arr.size() <= kInlineArrays) {  // written by the init kernel: no host copy, no stream sync
+        ia.inline_count = (uint32_t)arr.size();
+        for (size_t i = 0; i < arr.size(); ++i) ia.inline_arrays[i] = arr[i];
+    } else if (cudaMemcpyAsync(d_arr, arr.data(), sizeof(ArrayDesc) * arr.size(), cudaMemcpyHostToDevice,
+                               stream) != cudaSuccess) {
         return RIP_ECUDA;
+    }
 
     uint32_t* counts = reinterpret_cast<uint32_t*>(wsp + lay.counts);
     Lists lists{};
@@ -345,7 +353,14 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
     uint64_t* pool_used = reinterpret_cast<uint64_t*>(wsp + lay.pool_used);
     uint32_t launches = 0;
 
-    InitArgs ia{d_arr, (uint32_t)arr.size(), dplan, ds->status, lists, lay.small_max_m, counters, pool_used};
+    ia.arrays = d_arr;
+    ia.narrays = (uint32_t)arr.size();
+    ia.plan = dplan;
+    ia.status = ds->status;
+    ia.lists = lists;
+    ia.small_max_m = lay.small_max_m;
+    ia.counters = counters;
+    ia.pool_used = pool_used;
     if (launch_init(ia, stream) != cudaSuccess) return RIP_ECUDA;
     ++launches;
 

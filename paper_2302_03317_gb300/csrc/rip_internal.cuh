@@ -121,8 +121,12 @@ struct SmallArgs {
     uint32_t medium;
 };
 
+constexpr uint32_t kInlineArrays = 4;
+
 struct InitArgs {
-    const ArrayDesc* arrays;
+    ArrayDesc* arrays;
+    ArrayDesc inline_arrays[kInlineArrays];  // copied to `arrays` by the init kernel when used
+    uint32_t inline_count;
     uint32_t narrays;
     DevPlan plan;
     Status* status;

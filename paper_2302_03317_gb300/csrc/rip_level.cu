@@ -83,6 +83,7 @@ __global__ void init_kernel(InitArgs a) {
         *a.lists.bigfy_count = 0;
         for (int i = 0; i < 8; ++i) a.counters[i] = 0;
         *a.pool_used = 0;
+        for (uint32_t i = 0; i < a.inline_count; ++i) a.arrays[i] = a.inline_arrays[i];
     }
     __syncthreads();
     for (uint32_t i = tid; i < a.narrays; i += gridDim.x * blockDim.x) {
@@ -383,6 +384,10 @@ __global__ void scan_kernel(LevelArgs a, uint32_t small_max_m) {
         const ArrayDesc ad = a.arrays[S.arr];
         const uint32_t nt = (uint32_t)(a.T >= S.m ? 1 : (S.m + a.T - 1) / a.T);
         const uint32_t tb = a.sp_tile_begin[sp];
+        if ((uint64_t)tb + nt > a.counters[0]) {  // tile list overflowed (reported by tiles_kernel)
+            if (threadIdx.x == 0) report(a.status, RIP_EWORKSPACE, 0x6102, tb);
+            continue;
+        }
         for (uint32_t b = threadIdx.x; b < k; b += blockDim.x) {
             uint64_t size = 0;
             uint32_t fsum = 0, rsum = 0;
