@@ -165,7 +165,8 @@ Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& 
     for (const LevelCaps& c : caps) {
         L.big_cap = std::max(L.big_cap, c.big);
         L.tile_cap = (uint32_t)std::max<uint64_t>(L.tile_cap, c.tiles);
-        L.pool_cap = std::max(L.pool_cap, c.pool);
+        // each tile's tails and each demoted block are separate 16-byte-rounded allocations
+        L.pool_cap = std::max(L.pool_cap, c.pool + (c.tiles + c.dem) * (16 / std::min<uint32_t>(w, 16)));
         L.dem_cap = (uint32_t)std::max<uint64_t>(L.dem_cap, c.dem);
     }
     const uint64_t per_level_small = std::max<uint64_t>(narr, max_children);
@@ -417,6 +418,7 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
         a.words = reinterpret_cast<uint32_t*>(wsp + lay.words);
         a.pool = wsp + lay.pool;
         a.pool_cap = lay.pool_cap;
+        a.pool_align = 16 / std::min<uint32_t>(w, 16);
         a.dem = reinterpret_cast<DemRec*>(wsp + lay.dem);
         a.dem_cap = lay.dem_cap;
         if (launch_level(a, w, ds->num_sms, stream, &launches) != cudaSuccess) return RIP_ECUDA;

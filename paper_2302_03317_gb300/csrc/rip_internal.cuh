@@ -104,7 +104,8 @@ struct LevelArgs {
     ChildInfo* child;       // big_cap x k
     uint32_t* words;
     char* pool;
-    uint64_t pool_cap;  // elements
+    uint64_t pool_cap;    // elements
+    uint32_t pool_align;  // elements per 16 bytes: every pool allocation is a multiple of this
     DemRec* dem;
     uint32_t dem_cap;
 };

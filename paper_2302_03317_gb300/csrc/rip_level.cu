@@ -188,6 +188,13 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
         const uint64_t hs0 = ad.slot_base + alo / B;
         if (alo % B != 0 && tid == 0) report(a.status, RIP_EINTERNAL, 0x6201, alo);
 
+        // Slots of this level's grid inside the leading wrap piece [o, o+eps) lie in the
+        // region but in no tile's home range (only when B is smaller than the parent's):
+        // mark them empty so the permutation may fill them.
+        if (tr.t == 0 && S.eps >= B) {
+            const uint64_t first = (S.o + B - 1) / B, last = (S.o + S.eps) / B;
+            for (uint64_t g = first + tid; g < last; g += blockDim.x) a.words[ad.slot_base + g] = 0u;
+        }
         for (uint32_t b = tid; b < k; b += blockDim.x) sh.run[b] = 0;
         for (uint32_t j = tid; j < nwr * k; j += blockDim.x) sh.tbl[j] = 0;
         if (tid == 0) {
@@ -250,7 +257,9 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                     const uint32_t ndem = hs + nb > first_dem ? hs + nb - first_dem : 0;
                     uint64_t pool_off = 0;
                     if (ndem) {
-                        pool_off = atomicAdd((unsigned long long*)a.pool_used, (unsigned long long)ndem * B);
+                        // pool allocations stay 16-byte aligned: blocks are copied with 16-byte vectors
+                        const uint64_t bytes_el = ((uint64_t)ndem * B + a.pool_align - 1) / a.pool_align * a.pool_align;
+                        pool_off = atomicAdd((unsigned long long*)a.pool_used, (unsigned long long)bytes_el);
                         if (pool_off + (uint64_t)ndem * B > a.pool_cap) report(a.status, RIP_EWORKSPACE, 0x6202, pool_off);
                         sh.dfirst[b] = first_dem;
                         sh.dbase[b] = pool_off;
@@ -312,6 +321,10 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                     if (h >= H && poff + B > a.pool_cap) continue;  // reported at allocation
                     T* dst = h < H ? base + alo + (uint64_t)h * B : reinterpret_cast<T*>(a.pool) + poff;
                     const T* src = buf + b * B;
+                    if (a.vec16 && W < 16 && (reinterpret_cast<uintptr_t>(dst) & 15u)) {
+                        if (lane == 0) report(a.status, RIP_EINTERNAL, 0x6206, reinterpret_cast<uintptr_t>(dst));
+                        continue;
+                    }
                     if (a.vec16 && W < 16) {
                         const uint32_t units = B * W / 16u;
                         for (uint32_t u = lane; u < units; u += 32u)
@@ -350,7 +363,8 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
             if (i0 < k) sh.hsb[i0] = ex;
             if (i1 < k) sh.hsb[i1] = ex + r0;
             if (tid == 0) {
-                const uint64_t pb = atomicAdd((unsigned long long*)a.pool_used, (unsigned long long)total);
+                const uint64_t alloc = ((uint64_t)total + a.pool_align - 1) / a.pool_align * a.pool_align;
+                const uint64_t pb = atomicAdd((unsigned long long*)a.pool_used, (unsigned long long)alloc);
                 if (pb + total > a.pool_cap) report(a.status, RIP_EWORKSPACE, 0x6205, pb);
                 sh.pool_base = pb;
             }
@@ -455,7 +469,8 @@ __global__ void resolve_kernel(LevelArgs a) {
                 if (d > kWordDestMask) report(a.status, RIP_EINVAL, 0x6301, d);
                 nw = kWordOcc | (uint32_t)d;
             } else {
-                const uint64_t off = atomicAdd((unsigned long long*)a.pool_used, (unsigned long long)B);
+                const uint64_t alloc = ((uint64_t)B + a.pool_align - 1) / a.pool_align * a.pool_align;
+                const uint64_t off = atomicAdd((unsigned long long*)a.pool_used, (unsigned long long)alloc);
                 if (off + B > a.pool_cap) report(a.status, RIP_EWORKSPACE, 0x6302, off);
                 const uint32_t rec = atomicAdd(&a.counters[2], 1u);
                 if (rec < a.dem_cap)
@@ -513,7 +528,6 @@ __global__ void __launch_bounds__(kPermuteThreads) permute_kernel(LevelArgs a, u
     char* abase = nullptr;
     uint64_t aslot = 0, anslots = 0;
     uint64_t c = 0, cend = 0;
-    uint32_t spins = 0;
 
     for (;;) {
         if (!carrying) {
@@ -556,6 +570,10 @@ __global__ void __launch_bounds__(kPermuteThreads) permute_kernel(LevelArgs a, u
                 continue;
             }
             const U* sp = reinterpret_cast<const U*>(abase + (s - aslot) * slot_bytes);
+            if (reinterpret_cast<uintptr_t>(sp) % sizeof(U)) {  // claimed but unmovable: report
+                if (leader) report(a.status, RIP_EINTERNAL, 0x6407, s);
+                continue;
+            }
             for (uint32_t u = lg; u < units; u += kGroup) buf[u] = ld_cg(sp + u);
             __syncwarp(gmask);
             if (leader) {
@@ -574,7 +592,7 @@ __global__ void __launch_bounds__(kPermuteThreads) permute_kernel(LevelArgs a, u
                 continue;
             }
             const DemRec rec = a.dem[dw & kWordDestMask];
-            if (rec.pool_off + a.B > a.pool_cap) {
+            if (rec.pool_off + a.B > a.pool_cap || ((rec.pool_off * w) % sizeof(U)) != 0) {
                 if (leader) report(a.status, RIP_EINTERNAL, 0x6405, rec.pool_off);
                 carrying = false;
                 continue;
@@ -592,6 +610,11 @@ __global__ void __launch_bounds__(kPermuteThreads) permute_kernel(LevelArgs a, u
             continue;
         }
         U* dp = reinterpret_cast<U*>(abase + (d - aslot) * slot_bytes);
+        if (reinterpret_cast<uintptr_t>(dp) % sizeof(U)) {
+            if (leader) report(a.status, RIP_EINTERNAL, 0x6406, d);
+            carrying = false;
+            continue;
+        }
         U y[4];
 #pragma unroll
         for (uint32_t j = 0; j < 4; ++j) {
@@ -601,8 +624,10 @@ __global__ void __launch_bounds__(kPermuteThreads) permute_kernel(LevelArgs a, u
         uint32_t old = 0;
         if (leader) old = atom_or_acqrel(&a.words[d], kWordTaken);
         old = __shfl_sync(gmask, old, leader_lane);
+        __syncwarp(gmask);  // order the group's accesses to d after the leader's acquire
         if (old & kWordTaken) {
-            // a chain start holds the slot: wait until it has read it out
+            // a chain start holds the slot: wait (bounded) until it has read it out
+            uint32_t spins = 0;
             if (leader) {
                 while (ld_acquire(&a.words[d]) != 0u) {
                     if (++spins > (1u << 24)) {
