@@ -59,7 +59,7 @@ SMEM_DEEP = rip.Plan(ks=[4], Ts=[1 << 20], Bs=[8], base=16)
 INPLACE1 = rip.Plan(ks=[64], Ts=[4096], Bs=[256], base=4096)
 INPLACE2 = rip.Plan(ks=[16], Ts=[65536], Bs=[64], base=4096)
 TINY = rip.Plan(ks=[2], Ts=[8], Bs=[2], base=3)
-MIXED = rip.Plan(ks=[8, 4], Ts=[3000, 1 << 20], Bs=[6, 3], base=50)
+MIXED = rip.Plan(ks=[8, 4], Ts=[3000, 3 << 18], Bs=[6, 3], base=50)
 CFG1 = rip.Plan(ks=[64], Ts=[4096], Bs=[256], base=4096, max_levels=1)
 
 
