@@ -1,0 +1,317 @@
+#!/usr/bin/env python
+"""Benchmark: in-place shuffle of 2^30 u64 (iota) on GB300 through the C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one complete in-place shuffle (every scatter level, the on-SM
+solver and the Fisher-Yates leaves) of the resident 8 GiB array with the
+library's default plan (k = 256, base 4096).  Prints one JSON line (rank 0):
+value = shuffled elements per second over all ranks; "roofline" for the
+dominant kernel (algorithmic bytes / CUDA-event launch time vs the measured
+HBM copy bandwidth); "cpu_baseline" = the CPU oracle on a bounded sample;
+"e2e" = the same shuffle with the array copied from and back to pinned host
+memory inside the timed region.  N > 1: one independent replica per GPU
+(the method does not exchange data between GPUs in this build), launched
+with torchrun; the timed region is bracketed by barriers and the slowest
+rank's time is used.
+
+--impl reference times the CPU oracle (the only reference implementation of
+this method here) on a bounded sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "shuffled elems/s and % HBM roofline (2^30 u64); batched vs plain elems/s"
+UNIT = "elems/s"
+N_LOG2 = 30
+ELEM_BYTES = 8
+SEED = 1
+
+
+def _measured_hbm_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [ln.strip().split(", ") for ln in self.file.read().splitlines() if ln.strip()]
+        self.file.close()
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_sample(plan, log2n: int):
+    """Times the CPU oracle (single thread, as it stands) on 2^log2n u64 iota."""
+    import numpy as np
+
+    import oracle
+    n = 1 << log2n
+    a = np.arange(n, dtype=np.uint64)
+    op = oracle.Plan(list(plan.ks), list(plan.Ts), list(plan.Bs), plan.base, plan.max_levels)
+    t0 = time.perf_counter()
+    oracle.shuffle(a, SEED, op, inplace=True)
+    dt = time.perf_counter() - t0
+    return n / dt, dt, n
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import paper_2302_03317_gb300 as rip
+    n = 1 << N_LOG2
+    plan = rip.rip_default_plan(n, ELEM_BYTES)
+    sample_log2 = args.ref_sample_log2
+    for _ in range(args.warmup):
+        cpu_oracle_sample(plan, min(sample_log2, 18))
+    times = []
+    for _ in range(args.steps):
+        _, dt, ns = cpu_oracle_sample(plan, sample_log2)
+        times.append(dt)
+    rate = ns * len(times) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"in-place shuffle of 2^{N_LOG2} u64 iota (default plan, seed {SEED}); "
+                               f"each step the CPU oracle on a 2^{sample_log2} sample with the same plan",
+                   "sample_elems": ns},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"2^{sample_log2} u64 iota, same plan, single thread"},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--log2n", type=int, default=N_LOG2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-log2", type=int, default=26)
+    ap.add_argument("--ref-sample-log2", type=int, default=22)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import paper_2302_03317_gb300 as rip
+    from paper_2302_03317_gb300.inputs import fill_iota_
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    n = 1 << args.log2n
+    w = ELEM_BYTES
+    plan = rip.rip_default_plan(n, w)
+    x = torch.empty(n, dtype=torch.int64, device="cuda")
+    fill_iota_(x, w)
+    stream = torch.cuda.current_stream()
+
+    for i in range(args.warmup):
+        rip.shuffle_(x, SEED + i, plan=plan)
+    rc = rip.rip_get_device_status(stream.cuda_stream)
+    if rc != 0:
+        raise SystemExit(f"device status after warm-up: {rip.rip_strerror(rc)}")
+    info = rip.rip_last_call_info()
+
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    barrier()
+    clocks.start()
+    time.sleep(0.3)  # let the sampler start before the timed region
+    rip.rip_profile_reset()
+    rip.rip_profile_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    for i in range(args.steps):
+        rip.shuffle_(x, SEED + 1000 + i, plan=plan)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    rip.rip_profile_enable(False)
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    rc = rip.rip_get_device_status(stream.cuda_stream)
+    if rc != 0:
+        raise SystemExit(f"device status after timed steps: {rip.rip_strerror(rc)}")
+    prof = rip.rip_profile_get()
+    t_max = ms_total
+    if dist is not None:
+        tt = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    ms_per_step = t_max / args.steps
+    value = ws * n / (ms_per_step / 1e3)
+
+    # roofline of the dominant kernel: algorithmic bytes = one read + one write of
+    # every element the launch processes (each of these kernels touches the whole
+    # array once per launch for this workload)
+    hbm_gbs, peak_kind = _measured_hbm_gbs()
+    heavy = {k: v for k, v in prof.items() if k in ("classify", "permute", "solve_small", "solve_medium")}
+    dom = max(heavy.items(), key=lambda kv: kv[1][1]) if heavy else None
+    roof = None
+    if dom:
+        name, (launches, total_ms) = dom
+        avg_ms = total_ms / max(launches, 1)
+        alg_bytes = 2 * n * w
+        achieved = alg_bytes / (avg_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s",
+                "frac": achieved / hbm_gbs, "traffic": None, "peak_kind": peak_kind,
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms}
+    # whole-shuffle roofline: one read + one write per scatter level plus one for Fisher-Yates
+    scatter_levels, m_exp = 0, float(n)
+    while m_exp > plan.base and (plan.max_levels == 0 or scatter_levels < plan.max_levels):
+        m_exp /= plan.ks[min(scatter_levels, len(plan.ks) - 1)]
+        scatter_levels += 1
+    whole_roof_ms = (scatter_levels + 1) * 2 * n * w / (hbm_gbs * 1e9) * 1e3
+    kernel_table = {k: {"launches": v[0], "ms_per_step": v[1] / args.steps} for k, v in sorted(prof.items())}
+
+    # end to end through the C ABI: pinned host array -> device, shuffle, -> host
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty(n, dtype=torch.int64, pin_memory=True)
+        host.copy_(x)
+        torch.cuda.synchronize()
+        barrier()
+        h0 = torch.cuda.Event(enable_timing=True)
+        h1 = torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        for i in range(args.steps):
+            x.copy_(host, non_blocking=True)
+            rip.shuffle_(x, SEED + 2000 + i, plan=plan)
+            host.copy_(x, non_blocking=True)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        e_ms = h0.elapsed_time(h1) / args.steps
+        if dist is not None:
+            tt = torch.tensor([e_ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e_ms = float(tt.item())
+        e2e = {"value": ws * n / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": n * w,
+               "d2h_bytes_per_step": n * w, "ms_per_step": e_ms}
+        del host
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, dt, ns = cpu_oracle_sample(plan, args.cpu_sample_log2)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"2^{args.cpu_sample_log2} u64 iota with the same plan (one shuffle, {dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"in-place shuffle of 2^{args.log2n} u64 iota per GPU, default plan",
+                       "n": n, "elem_bytes": w, "seed": SEED,
+                       "plan": {"k": list(plan.ks), "T": list(plan.Ts), "B": list(plan.Bs), "base": plan.base,
+                                "max_levels": plan.max_levels},
+                       "inplace_levels": info["inplace_levels"], "aux_bytes": info["aux_bytes"],
+                       "aux_frac": info["aux_bytes"] / (n * w),
+                       "l2": "inputs larger than L2 (8 GiB array vs 129 MB L2)",
+                       "parallelism": f"replicas{ws}" if ws > 1 else "single"},
+            "roofline": roof,
+            "whole_shuffle_roofline_frac": whole_roof_ms / ms_per_step,
+            "scatter_levels": scatter_levels,
+            "kernels": kernel_table,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": info["launches"] * args.steps,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -139,6 +139,17 @@ const char *rip_strerror(int code);
  * Returns RIP_EINVAL if out is NULL. */
 int rip_last_call_info(uint64_t out[3]);
 
+/* Kernel timing (the measurement side of the library, no counterpart in the
+ * paper, which reports wall-clock means only, Sec. 6): while enabled, every
+ * kernel launch of later calls is bracketed by two CUDA events recorded on the
+ * launching stream.  rip_profile_get (call after synchronising the stream)
+ * returns, for the idx-th kernel name in alphabetical order, the launches and
+ * the summed event time in milliseconds; RIP_EINVAL when idx is past the
+ * last name.  Not thread-safe; intended for benchmarks. */
+int rip_profile_enable(int on);
+int rip_profile_reset(void);
+int rip_profile_get(uint32_t idx, const char **name, uint64_t *launches, double *total_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -65,6 +65,8 @@ def _load():
         lib.oracle_scatter_level.restype = i32
         lib.oracle_shuffle.argtypes = [vp, u64, u32, u64, u32, vp, vp, vp, u64, u32]
         lib.oracle_shuffle.restype = i32
+        lib.oracle_shuffle_sub.argtypes = [vp, u64, u32, u64, u64, u32, u32, vp, vp, vp, u64, u32]
+        lib.oracle_shuffle_sub.restype = i32
         lib.oracle_shuffle_batched.argtypes = [vp, vp, u32, u32, u64, u32, vp, vp, vp, u64, u32]
         lib.oracle_shuffle_batched.restype = i32
         lib.oracle_shuffle_many.argtypes = [vp, u64, u32, u64, u64, u32, vp, vp, vp, u64, u32, vp]
@@ -166,6 +168,38 @@ def shuffle(a: np.ndarray, seed: int, plan: Plan, inplace: bool = False) -> np.n
                                 plan.max_levels)
     if rc:
         raise RuntimeError("oracle_shuffle failed (invalid plan or out of memory)")
+    return a
+
+
+def shuffle_sub(a: np.ndarray, seed: int, o: int, level: int, plan: Plan) -> None:
+    """In place: the remaining recursion of the subproblem a (logical offset o, level)."""
+    assert a.flags.c_contiguous
+    ks, Ts, Bs = plan.arrays()
+    rc = _load().oracle_shuffle_sub(a.ctypes.data, a.shape[0], _elem_bytes(a), seed, o, level, len(ks),
+                                    ks.ctypes.data, Ts.ctypes.data, Bs.ctypes.data, plan.base, plan.max_levels)
+    if rc:
+        raise RuntimeError("oracle_shuffle_sub failed")
+
+
+def shuffle_parallel(a: np.ndarray, seed: int, plan: Plan, threads: int = 0) -> np.ndarray:
+    """Same result as shuffle(): the root level runs first, then its children
+    (independent subproblems, Sec. 4) run on a thread pool; in place."""
+    from concurrent.futures import ThreadPoolExecutor
+    n = a.shape[0]
+    cap = plan.max_levels if plan.max_levels else 64
+    if n <= plan.base or cap == 0:
+        return shuffle(a, seed, plan, inplace=True)
+    li = 0
+    out, sizes = scatter_level(a, seed, 0, 0, plan.ks[li], plan.Ts[li], plan.Bs[li])
+    a[...] = out
+    del out
+    starts = np.concatenate([[0], np.cumsum(sizes.astype(np.int64))])
+    jobs = [(int(starts[b]), int(sizes[b])) for b in range(len(sizes)) if sizes[b] > 1]
+    threads = threads or os.cpu_count() or 1
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        futs = [ex.submit(shuffle_sub, a[s:s + m], seed, s, 1, plan) for s, m in jobs]
+        for f in futs:
+            f.result()
     return a
 
 

@@ -307,6 +307,29 @@ int oracle_shuffle(void *data, uint64_t n, uint32_t w, uint64_t seed, uint32_t n
     return shuffle_rec((unsigned char *)data, n, w, seed, 0, 0, &p);
 }
 
+/* The remaining recursion of one subproblem: data[0..m) sits at logical
+ * offset o and level L of its array (the children of a level are independent,
+ * Sec. 4, so callers may run several of these concurrently). */
+int oracle_shuffle_sub(void *data, uint64_t m, uint32_t w, uint64_t seed, uint64_t o, uint32_t level,
+                       uint32_t num_levels, const uint32_t *ks, const uint64_t *Ts, const uint32_t *Bs,
+                       uint64_t base, uint32_t max_levels)
+{
+    if (w < 1 || (m > 0 && !data)) return -1;
+    if (!plan_ok(num_levels, ks, Ts, Bs, base)) return -1;
+    oracle_plan_t p;
+    memset(&p, 0, sizeof(p));
+    p.num_levels = num_levels;
+    for (uint32_t l = 0; l < num_levels; ++l) {
+        p.k[l] = ks[l];
+        p.T[l] = Ts[l];
+        p.B[l] = Bs[l];
+    }
+    p.base = base;
+    p.max_levels = max_levels;
+    if (m <= 1) return 0;
+    return shuffle_rec((unsigned char *)data, m, w, seed, o, level, &p);
+}
+
 /* Batched form: array i (ptrs[i], ns[i] elements) is shuffled with seed
  * base_seed + i and positions relative to its own start. */
 int oracle_shuffle_batched(void *const *ptrs, const uint64_t *ns, uint32_t count, uint32_t w,

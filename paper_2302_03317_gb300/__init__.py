@@ -110,6 +110,13 @@ def _load():
         lib.rip_strerror.restype = ctypes.c_char_p
         lib.rip_last_call_info.argtypes = [ctypes.POINTER(u64)]
         lib.rip_last_call_info.restype = i32
+        lib.rip_profile_enable.argtypes = [i32]
+        lib.rip_profile_enable.restype = i32
+        lib.rip_profile_reset.argtypes = []
+        lib.rip_profile_reset.restype = i32
+        lib.rip_profile_get.argtypes = [u32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(u64),
+                                        ctypes.POINTER(ctypes.c_double)]
+        lib.rip_profile_get.restype = i32
         _lib = lib
         return lib
 
@@ -187,6 +194,30 @@ def rip_last_call_info() -> dict:
     out = (ctypes.c_uint64 * 3)()
     _check(_load().rip_last_call_info(out), "rip_last_call_info")
     return {"aux_bytes": int(out[0]), "inplace_levels": int(out[1]), "launches": int(out[2])}
+
+
+def rip_profile_enable(on: bool) -> None:
+    _check(_load().rip_profile_enable(1 if on else 0), "rip_profile_enable")
+
+
+def rip_profile_reset() -> None:
+    _check(_load().rip_profile_reset(), "rip_profile_reset")
+
+
+def rip_profile_get() -> dict:
+    """{kernel name: (launches, total milliseconds)}; synchronise the stream first."""
+    lib = _load()
+    out = {}
+    i = 0
+    while True:
+        name = ctypes.c_char_p()
+        launches = ctypes.c_uint64()
+        ms = ctypes.c_double()
+        if lib.rip_profile_get(i, ctypes.byref(name), ctypes.byref(launches), ctypes.byref(ms)) != RIP_OK:
+            break
+        out[name.value.decode()] = (int(launches.value), float(ms.value))
+        i += 1
+    return out
 
 
 # ----------------------------------------------------------------- torch conveniences

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "rip_internal.cuh"
@@ -13,6 +14,74 @@
 namespace rip {
 
 __device__ Status g_status;  // device status word of this library, per device
+
+// ----------------------------------------------------------------- kernel timing
+namespace {
+struct ProfRec {
+    const char* name;
+    cudaEvent_t start, stop;
+};
+struct Profiler {
+    bool on = false;
+    std::vector<ProfRec> open;  // recorded, not yet folded into totals
+    std::vector<cudaEvent_t> spare;
+    std::vector<const char*> stack;
+    std::vector<cudaEvent_t> start_stack;
+    struct Tot {
+        std::string name;
+        uint64_t launches = 0;
+        double ms = 0;
+    };
+    std::vector<Tot> totals;
+    cudaEvent_t get() {
+        if (!spare.empty()) {
+            cudaEvent_t e = spare.back();
+            spare.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void fold() {
+        for (ProfRec& r : open) {
+            float ms = 0;
+            if (cudaEventSynchronize(r.stop) == cudaSuccess && cudaEventElapsedTime(&ms, r.start, r.stop) == cudaSuccess) {
+                auto it = std::find_if(totals.begin(), totals.end(), [&](const Tot& t) { return t.name == r.name; });
+                if (it == totals.end()) {
+                    totals.push_back(Tot{r.name, 0, 0});
+                    it = totals.end() - 1;
+                }
+                it->launches += 1;
+                it->ms += ms;
+            }
+            spare.push_back(r.start);
+            spare.push_back(r.stop);
+        }
+        open.clear();
+        std::sort(totals.begin(), totals.end(), [](const Tot& x, const Tot& y) { return x.name < y.name; });
+    }
+};
+Profiler g_prof;
+}  // namespace
+
+void prof_begin(const char* name, cudaStream_t s) {
+    if (!g_prof.on) return;
+    cudaEvent_t e = g_prof.get();
+    cudaEventRecord(e, s);
+    g_prof.stack.push_back(name);
+    g_prof.start_stack.push_back(e);
+}
+
+void prof_end(cudaStream_t s) {
+    if (!g_prof.on || g_prof.stack.empty()) return;
+    cudaEvent_t e = g_prof.get();
+    cudaEventRecord(e, s);
+    g_prof.open.push_back(ProfRec{g_prof.stack.back(), g_prof.start_stack.back(), e});
+    g_prof.stack.pop_back();
+    g_prof.start_stack.pop_back();
+    if (g_prof.open.size() > 4096) g_prof.fold();  // bounded event count
+}
 
 namespace {
 
@@ -547,6 +616,26 @@ const char* rip_strerror(int code) {
         case RIP_EINTERNAL: return "device-side consistency check failed";
         default: return "unknown error";
     }
+}
+
+int rip_profile_enable(int on) {
+    g_prof.on = on != 0;
+    return RIP_OK;
+}
+
+int rip_profile_reset(void) {
+    g_prof.fold();
+    g_prof.totals.clear();
+    return RIP_OK;
+}
+
+int rip_profile_get(uint32_t idx, const char** name, uint64_t* launches, double* total_ms) {
+    g_prof.fold();
+    if (idx >= g_prof.totals.size()) return RIP_EINVAL;
+    if (name) *name = g_prof.totals[idx].name.c_str();
+    if (launches) *launches = g_prof.totals[idx].launches;
+    if (total_ms) *total_ms = g_prof.totals[idx].ms;
+    return RIP_OK;
 }
 
 int rip_last_call_info(uint64_t out[3]) {

@@ -51,6 +51,7 @@ cudaError_t launch_digest(const void* data, uint64_t n, uint32_t w, unsigned lon
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const uint32_t grid = (uint32_t)(sms > 0 ? sms * 8 : 1024);
+    ProfScope p("digest", s);
     switch (w) {
         case 4: digest_kernel<4><<<grid, 256, 0, s>>>(data, n, out); break;
         case 8: digest_kernel<8><<<grid, 256, 0, s>>>(data, n, out); break;

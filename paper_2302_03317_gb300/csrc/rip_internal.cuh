@@ -137,6 +137,15 @@ struct InitArgs {
     uint64_t* pool_used;
 };
 
+// rip_api.cu: optional per-launch CUDA-event timing
+void prof_begin(const char* name, cudaStream_t s);
+void prof_end(cudaStream_t s);
+struct ProfScope {
+    cudaStream_t s;
+    ProfScope(const char* name, cudaStream_t st) : s(st) { prof_begin(name, st); }
+    ~ProfScope() { prof_end(s); }
+};
+
 // rip_small.cu
 size_t small_fixed_smem();
 size_t small_smem_bytes(uint64_t m, uint32_t w, bool medium);

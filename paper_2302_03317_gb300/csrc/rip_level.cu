@@ -800,6 +800,7 @@ size_t permute_smem_bytes(uint32_t B, uint32_t w) {
 }
 
 cudaError_t launch_init(const InitArgs& a, cudaStream_t s) {
+    ProfScope p("init", s);
     init_kernel<<<1, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -808,27 +809,50 @@ template <int W>
 static cudaError_t launch_level_w(const LevelArgs& a, uint32_t num_sms, cudaStream_t s, uint32_t* launches) {
     constexpr int E = W == 16 ? 4 : 8;
     cudaError_t err;
-    tiles_kernel<<<1, 1024, 0, s>>>(a);
+    {
+        ProfScope p("tiles", s);
+        tiles_kernel<<<1, 1024, 0, s>>>(a);
+    }
     const size_t csm = classify_smem_bytes(a.k, a.B, W);
     err = cudaFuncSetAttribute(classify_kernel<W, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
     if (err != cudaSuccess) return err;
-    classify_kernel<W, E><<<num_sms, kClassifyThreads, csm, s>>>(a);
-    scan_kernel<<<num_sms * 2, 512, 0, s>>>(a, a.small_max_m);
-    resolve_kernel<<<num_sms * 4, 256, 0, s>>>(a);
-    prefix_kernel<<<1, 1024, 0, s>>>(a);
+    {
+        ProfScope p("classify", s);
+        classify_kernel<W, E><<<num_sms, kClassifyThreads, csm, s>>>(a);
+    }
+    {
+        ProfScope p("scan", s);
+        scan_kernel<<<num_sms * 2, 512, 0, s>>>(a, a.small_max_m);
+    }
+    {
+        ProfScope p("resolve", s);
+        resolve_kernel<<<num_sms * 4, 256, 0, s>>>(a);
+    }
+    {
+        ProfScope p("prefix", s);
+        prefix_kernel<<<1, 1024, 0, s>>>(a);
+    }
     const size_t psm = permute_smem_bytes(a.B, W);
     if (a.vec16) {
         err = cudaFuncSetAttribute(permute_kernel<uint4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
         if (err != cudaSuccess) return err;
+        ProfScope p("permute", s);
         permute_kernel<uint4><<<num_sms * 8, kPermuteThreads, psm, s>>>(a, W);
     } else {
         using T = typename Elem<W>::T;
         err = cudaFuncSetAttribute(permute_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
         if (err != cudaSuccess) return err;
+        ProfScope p("permute", s);
         permute_kernel<T><<<num_sms * 8, kPermuteThreads, psm, s>>>(a, W);
     }
-    tails_kernel<W><<<num_sms * 4, 512, 0, s>>>(a);
-    demoted_kernel<W><<<num_sms, 256, 0, s>>>(a);
+    {
+        ProfScope p("tails", s);
+        tails_kernel<W><<<num_sms * 4, 512, 0, s>>>(a);
+    }
+    {
+        ProfScope p("demoted", s);
+        demoted_kernel<W><<<num_sms, 256, 0, s>>>(a);
+    }
     if (launches) *launches += 8;
     return cudaGetLastError();
 }
@@ -843,6 +867,7 @@ cudaError_t launch_level(const LevelArgs& a, uint32_t w, uint32_t num_sms, cudaS
 
 cudaError_t launch_bigfy(const Sub* list, const uint32_t* count, uint32_t cap, const ArrayDesc* arrays,
                          DevPlan plan, uint32_t w, const uint32_t* leftover, Status* status, cudaStream_t s) {
+    ProfScope p("bigfy", s);
     switch (w) {
         case 4: bigfy_kernel<4><<<8, 32, 0, s>>>(list, count, cap, arrays, plan, leftover, status); break;
         case 8: bigfy_kernel<8><<<8, 32, 0, s>>>(list, count, cap, arrays, plan, leftover, status); break;

@@ -306,6 +306,7 @@ size_t small_smem_bytes(uint64_t m, uint32_t w, bool medium) {
 
 cudaError_t launch_small(const SmallArgs& args, uint32_t w, size_t smem, uint32_t grid, cudaStream_t stream) {
     cudaError_t err;
+    ProfScope p(args.medium ? "solve_medium" : "solve_small", stream);
     switch (w) {
         case 4:
             err = cudaFuncSetAttribute(small_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -379,3 +379,14 @@ def test_golden_fixture(case):
     dtype = {4: np.uint32, 8: np.uint64}[w]
     got = oracle.shuffle(np.arange(n, dtype=dtype), seed, oracle.Plan(ks, Ts, Bs, base, max_levels))
     assert np.array_equal(got.astype(np.uint64), want)
+
+
+@pytest.mark.parametrize("plan", [PLANS[1], PLANS[3], oracle.Plan(ks=[8, 4], Ts=[3000, 3 << 18], Bs=[6, 3], base=50)])
+def test_threaded_children_equal_sequential(plan):
+    """Children of a level are independent subproblems (Sec. 4): running them on
+    threads after the root level gives the same array as the sequential oracle."""
+    a = np.arange(200_003, dtype=np.uint32)
+    want = oracle.shuffle(a, 17, plan)
+    got = a.copy()
+    oracle.shuffle_parallel(got, 17, plan, threads=4)
+    assert np.array_equal(got, want)
