@@ -163,6 +163,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-log2", type=int, default=26)
     ap.add_argument("--ref-sample-log2", type=int, default=22)
+    ap.add_argument("--ks", type=str, default="", help="profiling: comma list of k per level (overrides the default plan)")
+    ap.add_argument("--Bs", type=str, default="", help="profiling: comma list of B per level")
+    ap.add_argument("--Ts", type=str, default="", help="profiling: comma list of T per level")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -187,6 +190,11 @@ def main():
     n = 1 << args.log2n
     w = ELEM_BYTES
     plan = rip.rip_default_plan(n, w)
+    if args.ks:
+        ks = [int(v) for v in args.ks.split(",")]
+        Bs = [int(v) for v in args.Bs.split(",")] if args.Bs else [128 * 1024 // (k * w) for k in ks]
+        Ts = [int(v) for v in args.Ts.split(",")] if args.Ts else [(1 << 26) // b * b for b in Bs]
+        plan = rip.Plan(ks=ks, Ts=Ts, Bs=Bs, base=plan.base, max_levels=0)
     x = torch.empty(n, dtype=torch.int64, device="cuda")
     fill_iota_(x, w)
     stream = torch.cuda.current_stream()

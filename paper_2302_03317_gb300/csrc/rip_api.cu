@@ -100,7 +100,7 @@ struct LevelCaps {
 struct Layout {
     size_t total = 0;
     size_t arrays, lists_big0, lists_big1, small, medium, bigfy, counts, counters, pool_used;
-    size_t tiles, sp_tile_begin, C, FBc, TLc, tinfo, cand_prefix, child, words, pool, dem, mscratch;
+    size_t tiles, sp_tile_begin, C, FBc, TLc, tinfo, child, words, pool, dem, mscratch;
     uint32_t big_cap, small_cap, bigfy_cap, tile_cap, dem_cap, levels;
     uint64_t pair_cap, child_cap, pool_cap, slot_count;
     uint32_t small_max_m;
@@ -162,7 +162,7 @@ Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& 
     for (uint64_t n : ns) {
         nmax = std::max(nmax, n);
         nsum += n;
-        slots += (n + bmin - 1) / bmin;
+        slots += align_up((n + bmin - 1) / bmin, 64);  // each array's slot range starts at a multiple of 64
     }
     L.slot_count = slots;
     const uint32_t narr = (uint32_t)ns.size();
@@ -269,7 +269,6 @@ Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& 
     L.FBc = take(sizeof(uint32_t) * L.pair_cap);
     L.TLc = take(sizeof(uint32_t) * L.pair_cap);
     L.tinfo = take(sizeof(TileInfo) * L.tile_cap);
-    L.cand_prefix = take(sizeof(uint64_t) * (L.tile_cap + 1));
     L.child = take(sizeof(ChildInfo) * L.child_cap);
     L.words = take(L.levels ? sizeof(uint32_t) * L.slot_count : 0);
     L.pool = take(L.levels ? (size_t)w * L.pool_cap : 0);
@@ -390,7 +389,7 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
     bool aligned16 = true;
     for (size_t i = 0; i < ptrs.size(); ++i) {
         arr[i] = ArrayDesc{ptrs[i], ns[i] > 1 ? ns[i] : 0, base_seed + i, slot};
-        slot += (ns[i] + bmin - 1) / bmin;
+        slot += align_up((ns[i] + bmin - 1) / bmin, 64);
         aligned16 &= (reinterpret_cast<uintptr_t>(ptrs[i]) % 16) == 0;
     }
     ArrayDesc* d_arr = reinterpret_cast<ArrayDesc*>(wsp + lay.arrays);
@@ -432,6 +431,9 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
     ia.counters = counters;
     ia.pool_used = pool_used;
     if (launch_init(ia, stream) != cudaSuccess) return RIP_ECUDA;
+    // chain starts scan the whole slot table for words in state 01: start from all zero
+    if (lay.levels && cudaMemsetAsync(wsp + lay.words, 0, sizeof(uint32_t) * lay.slot_count, stream) != cudaSuccess)
+        return RIP_ECUDA;
     ++launches;
 
     auto run_small = [&]() -> int {
@@ -482,7 +484,9 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
         a.FBc = reinterpret_cast<uint32_t*>(wsp + lay.FBc);
         a.TLc = reinterpret_cast<uint32_t*>(wsp + lay.TLc);
         a.tinfo = reinterpret_cast<TileInfo*>(wsp + lay.tinfo);
-        a.cand_prefix = reinterpret_cast<uint64_t*>(wsp + lay.cand_prefix);
+        a.slot_count = lay.slot_count;
+        a.slot_chunks = (lay.slot_count + 63) / 64;
+        a.narrays = (uint32_t)arr.size();
         a.child = reinterpret_cast<ChildInfo*>(wsp + lay.child);
         a.words = reinterpret_cast<uint32_t*>(wsp + lay.words);
         a.pool = wsp + lay.pool;

@@ -97,6 +97,26 @@ __device__ __forceinline__ uint32_t warp_scatter_word(PhiloxKey key, uint32_t le
     return sel == 0 ? w0 : (sel == 1 ? w1 : (sel == 2 ? w2 : w3));
 }
 
+// Groups of 128 consecutive positions starting at a multiple of four: lane l
+// of the warp evaluates the Philox call of positions 4(Qg + l) .. 4(Qg + l) + 3,
+// all 32 lanes busy.  Step s (0..3) of the group covers positions
+// 4 Qg + 32 s + lane; group_step_word hands each lane the word of its position.
+__device__ __forceinline__ uint4 group_philox(PhiloxKey key, uint32_t level, uint64_t o, uint64_t Qg) {
+    const uint64_t q = Qg + (threadIdx.x & 31u);
+    return philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), level | (kTagScatter << 8), (uint32_t)o, key);
+}
+
+__device__ __forceinline__ uint32_t group_step_word(const uint4& r, uint32_t s) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const int src = (int)(8u * s + (lane >> 2));
+    const uint32_t w0 = __shfl_sync(0xffffffffu, r.x, src);
+    const uint32_t w1 = __shfl_sync(0xffffffffu, r.y, src);
+    const uint32_t w2 = __shfl_sync(0xffffffffu, r.z, src);
+    const uint32_t w3 = __shfl_sync(0xffffffffu, r.w, src);
+    const uint32_t sel = lane & 3u;
+    return sel == 0 ? w0 : (sel == 1 ? w1 : (sel == 2 ? w2 : w3));
+}
+
 __device__ __forceinline__ uint32_t bucket_of(uint32_t word, uint32_t k) { return __umulhi(word, k); }
 
 // Lemire acceptance for s in [1, 2^32]: returns true and sets v on accept.

@@ -6,7 +6,7 @@
 namespace rip {
 
 constexpr uint32_t kMaxK = 1024;
-constexpr uint32_t kSmallThreads = 1024;
+constexpr uint32_t kSmallThreads = 512;
 constexpr uint32_t kSmallCntCap = 512;    // (tile, bucket) counters of one in-SMEM scatter
 constexpr uint32_t kSmallTbl = 4096;      // (ranking warp, bucket) entries
 constexpr uint32_t kSmallStack = 256;     // pending scatter ranges inside one subproblem
@@ -93,16 +93,18 @@ struct LevelArgs {
     // tiles
     TileRef* tiles;
     uint32_t* sp_tile_begin;  // per big subproblem
-    uint32_t* counters;       // [0] tiles, [1] tile cursor, [2] demoted count, [4..5] candidate cursor
+    uint32_t* counters;       // [0] tiles, [1] tile cursor, [2] demoted count, [4..5] chunk cursor
     uint64_t* pool_used;
     uint32_t tile_cap;
     uint32_t* C;    // tile_cap x k counts
     uint32_t* FBc;  // tile_cap x k full blocks of earlier tiles
     uint32_t* TLc;  // tile_cap x k tail elements of earlier tiles
     TileInfo* tinfo;
-    uint64_t* cand_prefix;  // tile_cap + 1
     ChildInfo* child;       // big_cap x k
     uint32_t* words;
+    uint64_t slot_count;    // entries of the slot-word table
+    uint64_t slot_chunks;   // 64-entry chunks scanned for chain starts
+    uint32_t narrays;
     char* pool;
     uint64_t pool_cap;    // elements
     uint32_t pool_align;  // elements per 16 bytes: every pool allocation is a multiple of this

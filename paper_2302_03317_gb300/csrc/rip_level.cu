@@ -156,9 +156,16 @@ struct ClsShared {
     uint64_t pool_base;
 };
 
-template <int W, int E>
+// Element order inside a tile is its position order.  A round covers nwr * G
+// groups of 128 positions (aligned to multiples of four in the global position
+// space); ranking warp w owns groups w*G .. w*G+G-1 of the round, lane l of
+// step s holds position 4 Qg + 32 s + l.  Stable ranks: match_any inside a
+// step, a per-warp running count per bucket across the warp's steps, and one
+// exclusive prefix over the warps per bucket and round.
+template <int W, int G>
 __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs a) {
     using T = typename Elem<W>::T;
+    constexpr uint32_t E = 4 * G;  // elements per lane per round
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ClsShared& sh = *reinterpret_cast<ClsShared*>(smem_raw);
     T* buf = reinterpret_cast<T*>(smem_raw + ((sizeof(ClsShared) + 15) & ~size_t(15)));
@@ -166,7 +173,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t nwarps = blockDim.x >> 5;
     const uint32_t nwr = min(nwarps, kClsTbl / k);
-    const uint32_t round = nwr * 32u * E;
+    const uint32_t round = nwr * 128u * G;
     const uint32_t ntiles = a.counters[0];
     const uint32_t lt_mask = (1u << lane) - 1u;
 
@@ -186,6 +193,10 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
         const uint64_t avail = S.m > S.eps + lo ? min((uint64_t)r, S.m - S.eps - lo) : 0;
         const uint32_t H = (uint32_t)(avail / B);
         const uint64_t hs0 = ad.slot_base + alo / B;
+        const uint64_t P0 = S.o + lo;           // logical global position of the tile's first element
+        const uint32_t delta = (uint32_t)(P0 & 3u);
+        const uint64_t Q0 = P0 >> 2;
+        const uint32_t rv = r + delta;          // positions covered, counted from 4*Q0
         if (alo % B != 0 && tid == 0) report(a.status, RIP_EINTERNAL, 0x6201, alo);
 
         // Slots of this level's grid inside the leading wrap piece [o, o+eps) lie in the
@@ -205,30 +216,33 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
         if (warp < nwr) {
 #pragma unroll
             for (uint32_t e = 0; e < E; ++e) {
-                const uint32_t i = (warp * E + e) * 32u + lane;
-                if (i < r) nxt[e] = base[phys_index(S, lo + i)];
+                const uint32_t v = (warp * G + e / 4) * 128u + 32u * (e % 4) + lane;
+                if (v >= delta && v - delta < r) nxt[e] = base[phys_index(S, lo + (v - delta))];
             }
         }
         __syncthreads();
 
-        for (uint32_t R = 0; R < r; R += round) {
+        for (uint32_t R = 0; R < rv; R += round) {
             uint32_t bb[E], rk[E];
             if (warp < nwr) {
 #pragma unroll
                 for (uint32_t e = 0; e < E; ++e) val[e] = nxt[e];
-                if (R + round < r) {
+                if (R + round < rv) {
 #pragma unroll
                     for (uint32_t e = 0; e < E; ++e) {
-                        const uint32_t i = R + round + (warp * E + e) * 32u + lane;
-                        if (i < r) nxt[e] = base[phys_index(S, lo + i)];
+                        const uint32_t v = R + round + (warp * G + e / 4) * 128u + 32u * (e % 4) + lane;
+                        if (v - delta < r) nxt[e] = base[phys_index(S, lo + (v - delta))];
                     }
                 }
+                uint4 words[G];
+#pragma unroll
+                for (uint32_t g = 0; g < G; ++g)
+                    words[g] = group_philox(key, L, S.o, Q0 + (R >> 2) + (warp * G + g) * 32u);
 #pragma unroll
                 for (uint32_t e = 0; e < E; ++e) {
-                    const uint32_t ib = R + (warp * E + e) * 32u;
-                    const bool valid = ib + lane < r;
-                    const uint32_t word = warp_scatter_word(key, L, S.o, S.o + lo + ib);
-                    const uint32_t b = bucket_of(word, k);
+                    const uint32_t v = R + (warp * G + e / 4) * 128u + 32u * (e % 4) + lane;
+                    const bool valid = v >= delta && v - delta < r;
+                    const uint32_t b = bucket_of(group_step_word(words[e / 4], e % 4), k);
                     const uint32_t kk = valid ? b : 0xffffffffu;
                     const uint32_t peers = __match_any_sync(0xffffffffu, kk);
                     const uint32_t pre = valid ? sh.tbl[warp * k + b] : 0u;
@@ -242,10 +256,15 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
             }
             __syncthreads();
 
-            // per-bucket bookkeeping: completed blocks, home slots, demotion
+            // per bucket: exclusive prefix over the ranking warps (in place), completed
+            // blocks, home slots, demotion
             for (uint32_t b = tid; b < k; b += blockDim.x) {
                 uint32_t tot = 0;
-                for (uint32_t w = 0; w < nwr; ++w) tot += sh.tbl[w * k + b];
+                for (uint32_t w = 0; w < nwr; ++w) {
+                    const uint32_t c = sh.tbl[w * k + b];
+                    sh.tbl[w * k + b] = (uint16_t)tot;
+                    tot += c;
+                }
                 const uint32_t rb = sh.run[b], nr = rb + tot;
                 sh.newrun[b] = nr;
                 const uint32_t cb = rb / B, eb = nr / B;
@@ -258,8 +277,8 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                     uint64_t pool_off = 0;
                     if (ndem) {
                         // pool allocations stay 16-byte aligned: blocks are copied with 16-byte vectors
-                        const uint64_t bytes_el = ((uint64_t)ndem * B + a.pool_align - 1) / a.pool_align * a.pool_align;
-                        pool_off = atomicAdd((unsigned long long*)a.pool_used, (unsigned long long)bytes_el);
+                        const uint64_t alloc = ((uint64_t)ndem * B + a.pool_align - 1) / a.pool_align * a.pool_align;
+                        pool_off = atomicAdd((unsigned long long*)a.pool_used, (unsigned long long)alloc);
                         if (pool_off + (uint64_t)ndem * B > a.pool_cap) report(a.status, RIP_EWORKSPACE, 0x6202, pool_off);
                         sh.dfirst[b] = first_dem;
                         sh.dbase[b] = pool_off;
@@ -288,10 +307,8 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                 for (uint32_t e = 0; e < E; ++e) {
                     const uint32_t b = bb[e];
                     if (b == 0xffffffffu) continue;
-                    uint32_t cross = 0;
-                    for (uint32_t w = 0; w < warp; ++w) cross += sh.tbl[w * k + b];
                     const uint32_t rb = sh.run[b];
-                    const uint32_t rank = rb + cross + rk[e];
+                    const uint32_t rank = rb + sh.tbl[warp * k + b] + rk[e];
                     rk[e] = rank;
                     const uint32_t blk = rank / B, pos = rank - blk * B;
                     const uint32_t cb = rb / B, eb = sh.newrun[b] / B;
@@ -345,7 +362,6 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                     buf[b * B + rk[e] % B] = val[e];
                 }
             }
-            __syncthreads();
             for (uint32_t b = tid; b < k; b += blockDim.x) {
                 sh.run[b] = sh.newrun[b];
                 for (uint32_t w = 0; w < nwr; ++w) sh.tbl[w * k + b] = 0;
@@ -484,29 +500,6 @@ __global__ void resolve_kernel(LevelArgs a) {
     }
 }
 
-__global__ void prefix_kernel(LevelArgs a) {
-    __shared__ uint64_t scan64[32];
-    __shared__ uint64_t carry;
-    const uint32_t ntiles = a.counters[0];
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (uint32_t c0 = 0; c0 < ntiles; c0 += blockDim.x) {
-        const uint32_t t = c0 + threadIdx.x;
-        const uint64_t v = t < ntiles ? a.tinfo[t].home_used : 0;
-        uint64_t total;
-        const uint64_t ex = block_exclusive_scan<uint64_t>(v, scan64, &total);
-        if (t < ntiles) a.cand_prefix[t] = carry + ex;
-        __syncthreads();
-        if (threadIdx.x == 0) carry += total;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        a.cand_prefix[ntiles] = carry;
-        a.counters[4] = 0;  // candidate cursor (64-bit, words 4..5)
-        a.counters[5] = 0;
-    }
-}
-
 // ------------------------------------------------------------------ permute
 
 template <typename U>
@@ -519,52 +512,55 @@ __global__ void __launch_bounds__(kPermuteThreads) permute_kernel(LevelArgs a, u
     const uint32_t leader_lane = (tid & 31u) & ~(kGroup - 1u);
     const bool leader = lg == 0;
     U* buf = reinterpret_cast<U*>(smem_raw) + (size_t)g * units;
-    const uint32_t ntiles = a.counters[0];
-    const uint64_t total = a.cand_prefix[ntiles];
     const uint64_t slot_bytes = (uint64_t)a.B * w;
 
     bool carrying = false;
     uint32_t dw = 0;
     char* abase = nullptr;
     uint64_t aslot = 0, anslots = 0;
-    uint64_t c = 0, cend = 0;
+    uint64_t chunk = ~0ull;   // current 64-slot chunk of start candidates
+    uint32_t cpos = 64;       // next candidate inside the chunk
+    uint32_t cw[8];           // the chunk's words, 8 per lane of the group (lane lg holds slots lg*8 ..)
 
     for (;;) {
         if (!carrying) {
-            if (c >= cend) {
+            if (cpos >= 64) {
                 uint64_t c0 = 0;
-                if (leader) c0 = atomicAdd((unsigned long long*)&a.counters[4], 32ull);
-                c0 = __shfl_sync(gmask, c0, leader_lane);
-                if (c0 >= total) break;
-                c = c0;
-                cend = min(c0 + 32, total);
-            }
-            uint32_t ok = 0, w0 = 0;
-            uint64_t s = 0;
-            if (leader) {
-                // tile of candidate c: last t with cand_prefix[t] <= c
-                uint32_t lo = 0, hi = ntiles;
-                while (hi - lo > 1) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (a.cand_prefix[mid] <= c) lo = mid; else hi = mid;
+                if (leader) c0 = atomicAdd((unsigned long long*)&a.counters[4], 1ull);
+                chunk = __shfl_sync(gmask, c0, leader_lane);
+                if (chunk >= a.slot_chunks) break;
+                const uint64_t s0 = chunk * 64u + lg * 8u;
+#pragma unroll
+                for (uint32_t j = 0; j < 8; ++j) cw[j] = s0 + j < a.slot_count ? ld_relaxed(&a.words[s0 + j]) : 0u;
+                cpos = 0;
+                // the array holding this chunk (array slot ranges start at multiples of 64)
+                uint32_t lo = 0, hi = a.narrays;
+                if (leader) {
+                    while (hi - lo > 1) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (a.arrays[mid].slot_base <= chunk * 64u) lo = mid; else hi = mid;
+                    }
                 }
-                const TileInfo ti = a.tinfo[lo];
-                s = ti.hs0 + (c - a.cand_prefix[lo]);
-                const ArrayDesc ad = a.arrays[a.big[a.tiles[lo].sp].arr];
+                lo = __shfl_sync(gmask, lo, leader_lane);
+                const ArrayDesc ad = a.arrays[lo];
                 abase = ad.data;
                 aslot = ad.slot_base;
                 anslots = ad.n / a.B;  // whole slots of the array
-                w0 = ld_relaxed(&a.words[s]);
-                if ((w0 >> 30) == 1u) ok = atomicCAS(&a.words[s], w0, w0 | kWordTaken) == w0;
             }
-            ++c;
+            // next candidate holding an unmoved block
+            const uint32_t owner = cpos >> 3;
+            uint32_t w0 = 0;
+#pragma unroll
+            for (uint32_t j = 0; j < 8; ++j)
+                if ((cpos & 7u) == j) w0 = cw[j];
+            w0 = __shfl_sync(gmask, w0, leader_lane + owner);
+            const uint64_t s = chunk * 64u + cpos;
+            ++cpos;
+            if ((w0 >> 30) != 1u) continue;
+            uint32_t ok = 0;
+            if (leader) ok = atomicCAS(&a.words[s], w0, w0 | kWordTaken) == w0;
             ok = __shfl_sync(gmask, ok, leader_lane);
             if (!ok) continue;
-            w0 = __shfl_sync(gmask, w0, leader_lane);
-            s = __shfl_sync(gmask, s, leader_lane);
-            abase = reinterpret_cast<char*>(__shfl_sync(gmask, reinterpret_cast<uint64_t>(abase), leader_lane));
-            aslot = __shfl_sync(gmask, aslot, leader_lane);
-            anslots = __shfl_sync(gmask, anslots, leader_lane);
             if (s < aslot || s - aslot >= anslots) {
                 if (leader) report(a.status, RIP_EINTERNAL, 0x6403, s);
                 continue;
@@ -807,7 +803,7 @@ cudaError_t launch_init(const InitArgs& a, cudaStream_t s) {
 
 template <int W>
 static cudaError_t launch_level_w(const LevelArgs& a, uint32_t num_sms, cudaStream_t s, uint32_t* launches) {
-    constexpr int E = W == 16 ? 4 : 8;
+    constexpr int E = W == 16 ? 1 : 2;  // groups of 128 positions per ranking warp per round
     cudaError_t err;
     {
         ProfScope p("tiles", s);
@@ -827,10 +823,6 @@ static cudaError_t launch_level_w(const LevelArgs& a, uint32_t num_sms, cudaStre
     {
         ProfScope p("resolve", s);
         resolve_kernel<<<num_sms * 4, 256, 0, s>>>(a);
-    }
-    {
-        ProfScope p("prefix", s);
-        prefix_kernel<<<1, 1024, 0, s>>>(a);
     }
     const size_t psm = permute_smem_bytes(a.B, W);
     if (a.vec16) {
@@ -853,7 +845,7 @@ static cudaError_t launch_level_w(const LevelArgs& a, uint32_t num_sms, cudaStre
         ProfScope p("demoted", s);
         demoted_kernel<W><<<num_sms, 256, 0, s>>>(a);
     }
-    if (launches) *launches += 8;
+    if (launches) *launches += 7;
     return cudaGetLastError();
 }
 

@@ -96,14 +96,23 @@ __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint3
     for (uint32_t j = tid; j < ncnt; j += blockDim.x) sh.thr[j] = 0;
     __syncthreads();
 
-    // counts per (tile, bucket)
-    for (uint32_t ib = warp * 32u; ib < len; ib += kWarps * 32u) {
-        const uint32_t i = ib + lane;
-        const uint32_t word = warp_scatter_word(key, L, o_r, o_r + ib);
-        const bool valid = i < len;
-        const uint32_t key2 = valid ? (i / T) * k + bucket_of(word, k) : 0xffffffffu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, key2);
-        if (valid && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&sh.thr[key2], (uint32_t)__popc(peers));
+    // counts per (tile, bucket); groups of 128 positions aligned to multiples of four
+    {
+        const uint32_t delta = (uint32_t)(o_r & 3u);
+        const uint64_t Q0 = o_r >> 2;
+        const uint32_t vlen = len + delta;
+        for (uint32_t gb = warp * 128u; gb < vlen; gb += kWarps * 128u) {
+            const uint4 rr = group_philox(key, L, o_r, Q0 + gb / 4u);
+#pragma unroll
+            for (uint32_t st = 0; st < 4; ++st) {
+                const uint32_t v = gb + 32u * st + lane;
+                const bool valid = v >= delta && v - delta < len;
+                const uint32_t b = bucket_of(group_step_word(rr, st), k);
+                const uint32_t key2 = valid ? ((v - delta) / T) * k + b : 0xffffffffu;
+                const uint32_t peers = __match_any_sync(0xffffffffu, key2);
+                if (valid && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&sh.thr[key2], (uint32_t)__popc(peers));
+            }
+        }
     }
     __syncthreads();
 
@@ -141,25 +150,30 @@ __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint3
     }
     __syncthreads();
 
-    // stable ranks inside each (tile, bucket), then the move X -> Y
+    // stable ranks inside each (tile, bucket), then the move X -> Y.  A round covers
+    // nwr groups of 128 positions; tbl[w][b] counts bucket b in warp w's group, then
+    // holds the element rank base (running count of the tile + earlier warps).
     const uint32_t nwr = min(kWarps, (uint32_t)kSmallTbl / k);
-    const uint32_t round = nwr * 32u * kE;
+    const uint32_t round = nwr * 128u;
     const uint32_t lt_mask = (1u << lane) - 1u;
     for (uint32_t t = 0; t < tiles; ++t) {
         const uint32_t lo = t * T, hi = min(lo + T, len);
+        const uint64_t P0 = o_r + lo;
+        const uint32_t delta = (uint32_t)(P0 & 3u);
+        const uint64_t Q0 = P0 >> 2;
+        const uint32_t tl = hi - lo, vlen = tl + delta;
         for (uint32_t b = tid; b < k; b += blockDim.x) sh.run[b] = 0;
         for (uint32_t j = tid; j < nwr * k; j += blockDim.x) sh.tbl[j] = 0;
         __syncthreads();
-        for (uint32_t R = lo; R < hi; R += round) {
-            uint32_t bb[kE], pr[kE];
+        for (uint32_t R = 0; R < vlen; R += round) {
+            uint32_t bb[4], pr[4];
             if (warp < nwr) {
+                const uint4 rr = group_philox(key, L, o_r, Q0 + (R >> 2) + warp * 32u);
 #pragma unroll
-                for (uint32_t e = 0; e < kE; ++e) {
-                    const uint32_t ib = R + (warp * kE + e) * 32u;
-                    const uint32_t i = ib + lane;
-                    const bool valid = i < hi;
-                    const uint32_t word = warp_scatter_word(key, L, o_r, o_r + ib);
-                    const uint32_t b = bucket_of(word, k);
+                for (uint32_t st = 0; st < 4; ++st) {
+                    const uint32_t v = R + warp * 128u + 32u * st + lane;
+                    const bool valid = v >= delta && v - delta < tl;
+                    const uint32_t b = bucket_of(group_step_word(rr, st), k);
                     const uint32_t kk = valid ? b : 0xffffffffu;
                     const uint32_t peers = __match_any_sync(0xffffffffu, kk);
                     const uint32_t pre = valid ? sh.tbl[warp * k + b] : 0u;
@@ -167,40 +181,44 @@ __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint3
                     if (valid && lane == (uint32_t)(__ffs(peers) - 1))
                         sh.tbl[warp * k + b] = (uint16_t)(pre + __popc(peers));
                     __syncwarp();
-                    bb[e] = valid ? b : 0xffffffffu;
-                    pr[e] = pre + __popc(peers & lt_mask);
+                    bb[st] = valid ? b : 0xffffffffu;
+                    pr[st] = pre + __popc(peers & lt_mask);
                 }
+            }
+            __syncthreads();
+            // rank bases: running count of the tile plus the counts of earlier warps
+            for (uint32_t b = tid; b < k; b += blockDim.x) {
+                uint32_t acc = sh.run[b];
+                for (uint32_t w = 0; w < nwr; ++w) {
+                    const uint32_t c = sh.tbl[w * k + b];
+                    sh.tbl[w * k + b] = (uint16_t)acc;
+                    acc += c;
+                }
+                sh.run[b] = acc;
             }
             __syncthreads();
             if (warp < nwr) {
 #pragma unroll
-                for (uint32_t e = 0; e < kE; ++e) {
-                    const uint32_t b = bb[e];
+                for (uint32_t st = 0; st < 4; ++st) {
+                    const uint32_t b = bb[st];
                     if (b == 0xffffffffu) continue;
-                    uint32_t cross = 0;
-                    for (uint32_t w = 0; w < warp; ++w) cross += sh.tbl[w * k + b];
-                    const uint32_t rank = sh.run[b] + cross + pr[e];
+                    const uint32_t rank = sh.tbl[warp * k + b] + pr[st];
                     const uint32_t ci = t * k + b;
                     const uint32_t d = rank < sh.thr[ci] ? sh.fb[ci] + rank : sh.tb[ci] + rank;
-                    const uint32_t i = R + (warp * kE + e) * 32u + lane;
+                    const uint32_t i = lo + (R + warp * 128u + 32u * st + lane - delta);
                     if (d >= len) {  // cannot happen for consistent counts; never write out of range
                         report(status, RIP_EINTERNAL, 0x5103, d);
                         continue;
                     }
                     Y[a + d] = X[a + i];
                 }
+                __syncwarp();
+                // each warp reads only its own row: clear it for the next round
+                for (uint32_t b = lane; b < k; b += 32u) sh.tbl[warp * k + b] = 0;
+                __syncwarp();
             }
-            __syncthreads();
-            for (uint32_t b = tid; b < k; b += blockDim.x) {
-                uint32_t tot = 0;
-                for (uint32_t w = 0; w < nwr; ++w) {
-                    tot += sh.tbl[w * k + b];
-                    sh.tbl[w * k + b] = 0;
-                }
-                sh.run[b] += tot;
-            }
-            __syncthreads();
         }
+        __syncthreads();
     }
 
     // children: leaves now, larger ones onto the stack
@@ -250,9 +268,22 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(SmallArgs args) {
         T* D = args.medium ? reinterpret_cast<T*>(args.gscratch + (uint64_t)blockIdx.x * args.gslot_bytes)
                            : reinterpret_cast<T*>(P1 + ((m + 7u) & ~7u));
 
-        for (uint32_t i = tid; i < m; i += blockDim.x) {
-            D[i] = base[phys_index(s, i)];
-            P0[i] = (uint16_t)i;
+        // load through the rotation, eight independent loads in flight per thread
+        for (uint32_t i0 = tid; i0 < m; i0 += 8u * blockDim.x) {
+            T v[8];
+#pragma unroll
+            for (uint32_t j = 0; j < 8; ++j) {
+                const uint32_t i = i0 + j * blockDim.x;
+                if (i < m) v[j] = base[phys_index(s, i)];
+            }
+#pragma unroll
+            for (uint32_t j = 0; j < 8; ++j) {
+                const uint32_t i = i0 + j * blockDim.x;
+                if (i < m) {
+                    D[i] = v[j];
+                    P0[i] = (uint16_t)i;
+                }
+            }
         }
         if (tid == 0) sh.stack_top = 0;
         __syncthreads();
