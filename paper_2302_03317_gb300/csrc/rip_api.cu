@@ -4,6 +4,7 @@
 // level are independent, so one launch processes all of them).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -86,6 +87,7 @@ void prof_end(cudaStream_t s) {
 namespace {
 
 constexpr uint32_t kMediumGrid = 16;
+constexpr uint32_t kParkAfter = 256;  // chain steps before the permutation parks a block
 constexpr size_t kClassifySmemBudget = 200 * 1024;
 
 struct LevelCaps {
@@ -100,8 +102,8 @@ struct LevelCaps {
 struct Layout {
     size_t total = 0;
     size_t arrays, lists_big0, lists_big1, small, medium, bigfy, counts, counters, pool_used;
-    size_t tiles, sp_tile_begin, C, FBc, TLc, tinfo, child, words, pool, dem, mscratch;
-    uint32_t big_cap, small_cap, bigfy_cap, tile_cap, dem_cap, levels;
+    size_t tiles, sp_tile_begin, C, FBc, TLc, tinfo, child, words, pool, dem, parks, mscratch;
+    uint32_t big_cap, small_cap, bigfy_cap, tile_cap, dem_cap, park_cap, levels;
     uint64_t pair_cap, child_cap, pool_cap, slot_count;
     uint32_t small_max_m;
     uint64_t aux_bytes;
@@ -145,6 +147,19 @@ int validate_plan(const rip_plan& p, uint32_t w) {
 }
 
 bool valid_w(uint32_t w) { return w == 4 || w == 8 || w == 16; }
+
+// Host check of the invariant-division constants against plain division.
+bool fastdiv_ok(const FastDiv& f) {
+    const uint32_t d = f.d;
+    const uint32_t ns[] = {0u, 1u, d - 1u, d, d + 1u, 2u * d - 1u, 2u * d, 12345678u, 0x7fffffffu,
+                           0x80000000u, 0xfffffffeu, 0xffffffffu, d * 1000u + 7u};
+    for (uint32_t n : ns) {
+        const uint32_t t = (uint32_t)(((uint64_t)f.m * n) >> 32);
+        const uint32_t q = (t + ((n - t) >> f.s1)) >> f.s2;
+        if (q != n / d) return false;
+    }
+    return true;
+}
 
 // Expected-size model of the recursion used to size the workspace.  A level
 // can hold subproblems too large for one SM when mu_L + 10 sqrt(mu_L) + 64
@@ -273,6 +288,8 @@ Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& 
     L.words = take(L.levels ? sizeof(uint32_t) * L.slot_count : 0);
     L.pool = take(L.levels ? (size_t)w * L.pool_cap : 0);
     L.dem = take(sizeof(DemRec) * L.dem_cap);
+    L.park_cap = L.levels ? (uint32_t)std::min<uint64_t>(65536, slots / 16 + 64) : 0;
+    L.parks = take(sizeof(ParkRec) * L.park_cap);
     L.mscratch = take((size_t)kMediumGrid * kMediumMaxM * w);
     L.total = off;
     (void)meta_start;
@@ -381,6 +398,9 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
     ds->last_info[0] = lay.aux_bytes;
 
     const DevPlan dplan = to_dev(plan);
+    // tuning knob: chain steps before the permutation parks a block (RIP_PARK_AFTER)
+    uint32_t park_after = kParkAfter;
+    if (const char* env = std::getenv("RIP_PARK_AFTER")) park_after = (uint32_t)std::strtoul(env, nullptr, 10);
     uint32_t bmin = 0xffffffffu;
     for (uint32_t l = 0; l < plan.num_levels; ++l) bmin = std::min(bmin, plan.level[l].block);
     // array table: device pointer, size, seed, slot base
@@ -460,6 +480,8 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
         a.k = plan.level[li].k;
         a.B = plan.level[li].block;
         a.T = plan.level[li].tile;
+        a.fdB = FastDiv::make(a.B);
+        if (!fastdiv_ok(a.fdB)) return RIP_EINTERNAL;
         a.vec16 = aligned16 && ((a.B * w) % 16 == 0) ? 1u : 0u;
         a.big = lists.big[lev & 1];
         a.big_count = lists.big_count[lev & 1];
@@ -494,6 +516,9 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
         a.pool_align = 16 / std::min<uint32_t>(w, 16);
         a.dem = reinterpret_cast<DemRec*>(wsp + lay.dem);
         a.dem_cap = lay.dem_cap;
+        a.parks = reinterpret_cast<ParkRec*>(wsp + lay.parks);
+        a.park_cap = lay.park_cap;
+        a.park_after = park_after;
         if (launch_level(a, w, ds->num_sms, stream, &launches) != cudaSuccess) return RIP_ECUDA;
         rc = run_small();
         if (rc) return rc;

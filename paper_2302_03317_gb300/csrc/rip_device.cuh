@@ -53,14 +53,12 @@ __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_
     uint32_t k0 = key.k0, k1 = key.k1;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c0;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
-        const uint32_t lo1 = 0xCD9E8D57u * c2;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
-        c0 = hi1 ^ c1 ^ k0;
-        c2 = hi0 ^ c3 ^ k1;
-        c1 = lo1;
-        c3 = lo0;
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0;  // one wide multiply gives hi and lo
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        c0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        c2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        c1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
@@ -172,6 +170,32 @@ struct FyStream {
         if (lemire_accept(pick(cached, (uint32_t)(p & 3u)), i + 1, v)) return v;
         return fy_draw_retry(key, level, o, p, i + 1);
     }
+};
+
+// ----------------------------------------------------------------- division by invariants
+
+// Unsigned 32-bit division by a run-time constant d >= 1 with one multiply-high
+// and shifts (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994, Fig. 4.1): l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1, q = (t + ((n - t) >> min(l,1))) >> max(l-1,0)
+// with t = mulhi(m, n); exact for every n < 2^32.
+struct FastDiv {
+    uint32_t d, m, s1, s2;
+    __host__ __device__ static FastDiv make(uint32_t div) {
+        FastDiv f;
+        f.d = div;
+        uint32_t l = 0;
+        while (l < 32 && (1ull << l) < div) ++l;
+        f.m = (uint32_t)(((1ull << 32) * ((1ull << l) - div)) / div + 1);
+        f.s1 = l < 1 ? l : 1;
+        f.s2 = l > 0 ? l - 1 : 0;
+        return f;
+    }
+    __device__ __forceinline__ uint32_t div(uint32_t n) const {
+        const uint32_t t = __umulhi(m, n);
+        return (t + ((n - t) >> s1)) >> s2;
+    }
+    __device__ __forceinline__ uint32_t mod(uint32_t n) const { return n - div(n) * d; }
 };
 
 // ----------------------------------------------------------------- plan / descriptors

@@ -55,6 +55,12 @@ struct DemRec {
     uint64_t pool_off;
 };
 
+// A block a chain put aside after too many steps; placed after the permutation.
+struct ParkRec {
+    uint64_t pool_off;  // element offset in the pool, ~0 when the park failed
+    uint64_t dst;       // destination address (byte pointer)
+};
+
 struct Lists {
     Sub* big[2];
     uint32_t* big_count[2];
@@ -75,6 +81,7 @@ struct LevelArgs {
     Status* status;
     uint32_t level, k, B, vec16;
     uint64_t T;
+    FastDiv fdB;  // division by B
     // this level's subproblems and the next level's
     const Sub* big;
     const uint32_t* big_count;
@@ -93,7 +100,7 @@ struct LevelArgs {
     // tiles
     TileRef* tiles;
     uint32_t* sp_tile_begin;  // per big subproblem
-    uint32_t* counters;       // [0] tiles, [1] tile cursor, [2] demoted count, [4..5] chunk cursor
+    uint32_t* counters;       // [0] tiles, [1] tile cursor, [2] demoted count, [4..5] chunk cursor, [6] parks
     uint64_t* pool_used;
     uint32_t tile_cap;
     uint32_t* C;    // tile_cap x k counts
@@ -110,6 +117,9 @@ struct LevelArgs {
     uint32_t pool_align;  // elements per 16 bytes: every pool allocation is a multiple of this
     DemRec* dem;
     uint32_t dem_cap;
+    ParkRec* parks;
+    uint32_t park_cap;
+    uint32_t park_after;  // chain steps before a carried block is parked
 };
 
 struct SmallArgs {

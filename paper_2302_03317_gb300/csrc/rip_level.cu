@@ -131,6 +131,7 @@ __global__ void tiles_kernel(LevelArgs a) {
         a.counters[3] = 0;
         a.counters[4] = 0;
         a.counters[5] = 0;
+        a.counters[6] = 0;
         *a.pool_used = 0;
         *a.next_big_count = 0;
         *a.small_count = 0;
@@ -144,6 +145,7 @@ struct ClsShared {
     uint32_t run[kMaxK];      // bucket elements seen in this tile
     uint32_t newrun[kMaxK];   // ... after the current round
     uint32_t hsb[kMaxK];      // home index of the first block completing this round
+    uint32_t binfo[kMaxK];    // per bucket this round: (run mod B) | (blocks completing) << 16
     uint32_t dfirst[kMaxK];   // first home index that is demoted, per bucket (this round)
     uint64_t dbase[kMaxK];    // pool offset of that demoted block
     uint16_t tbl[kClsTbl];    // (ranking warp, bucket) counts of the round
@@ -267,7 +269,9 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                 }
                 const uint32_t rb = sh.run[b], nr = rb + tot;
                 sh.newrun[b] = nr;
-                const uint32_t cb = rb / B, eb = nr / B;
+                const uint32_t cb = a.fdB.div(rb), eb = a.fdB.div(nr);
+                const uint32_t rem = rb - cb * B;
+                sh.binfo[b] = rem | ((eb - cb) << 16);
                 if (eb > cb) {
                     const uint32_t nb = eb - cb;
                     const uint32_t hs = atomicAdd(&sh.home_next, nb);
@@ -296,7 +300,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                                 report(a.status, RIP_EWORKSPACE, 0x6204, rec);
                         }
                     }
-                    if (rb % B != 0) sh.flist[atomicAdd(&sh.nflush, 1u)] = (uint16_t)b;
+                    if (rem != 0) sh.flist[atomicAdd(&sh.nflush, 1u)] = (uint16_t)b;
                 }
             }
             __syncthreads();
@@ -307,16 +311,17 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                 for (uint32_t e = 0; e < E; ++e) {
                     const uint32_t b = bb[e];
                     if (b == 0xffffffffu) continue;
-                    const uint32_t rb = sh.run[b];
-                    const uint32_t rank = rb + sh.tbl[warp * k + b] + rk[e];
-                    rk[e] = rank;
-                    const uint32_t blk = rank / B, pos = rank - blk * B;
-                    const uint32_t cb = rb / B, eb = sh.newrun[b] / B;
-                    if (blk < eb) {
-                        if (blk == cb && rb % B != 0) {
+                    // offset inside the bucket's current partial block, counted from its start
+                    const uint32_t bi = sh.binfo[b];
+                    const uint32_t rem = bi & 0xFFFFu;
+                    const uint32_t local = rem + sh.tbl[warp * k + b] + rk[e];
+                    const uint32_t q = a.fdB.div(local), pos = local - q * B;
+                    rk[e] = pos;
+                    if (q < (bi >> 16)) {
+                        if (q == 0 && rem != 0) {
                             buf[b * B + pos] = val[e];
                         } else {
-                            const uint32_t h = sh.hsb[b] + (blk - cb);
+                            const uint32_t h = sh.hsb[b] + q;
                             const uint64_t poff = sh.dbase[b] + (uint64_t)(h - sh.dfirst[b]) * B;
                             if (h >= H && poff + B > a.pool_cap) continue;  // reported at allocation
                             T* dst = h < H ? base + alo + (uint64_t)h * B : reinterpret_cast<T*>(a.pool) + poff;
@@ -359,7 +364,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                 for (uint32_t e = 0; e < E; ++e) {
                     const uint32_t b = bb[e];
                     if (b == 0xffffffffu) continue;
-                    buf[b * B + rk[e] % B] = val[e];
+                    buf[b * B + rk[e]] = val[e];
                 }
             }
             for (uint32_t b = tid; b < k; b += blockDim.x) {
@@ -373,7 +378,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
         // tails of every bucket -> pool; counts and tile info
         {
             const uint32_t i0 = 2 * tid, i1 = 2 * tid + 1;
-            const uint32_t r0 = i0 < k ? sh.run[i0] % B : 0, r1 = i1 < k ? sh.run[i1] % B : 0;
+            const uint32_t r0 = i0 < k ? a.fdB.mod(sh.run[i0]) : 0, r1 = i1 < k ? a.fdB.mod(sh.run[i1]) : 0;
             uint32_t total;
             const uint32_t ex = block_exclusive_scan<uint32_t>(r0 + r1, sh.scan, &total);
             if (i0 < k) sh.hsb[i0] = ex;
@@ -389,7 +394,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
             if (pb + total <= a.pool_cap) {
                 T* pool = reinterpret_cast<T*>(a.pool);
                 for (uint32_t b = warp; b < k; b += nwarps) {
-                    const uint32_t R = sh.run[b] % B;
+                    const uint32_t R = a.fdB.mod(sh.run[b]);
                     for (uint32_t j = lane; j < R; j += 32u) pool[pb + sh.hsb[b] + j] = buf[b * B + j];
                 }
             }
@@ -503,7 +508,7 @@ __global__ void resolve_kernel(LevelArgs a) {
 // ------------------------------------------------------------------ permute
 
 template <typename U>
-__global__ void __launch_bounds__(kPermuteThreads) permute_kernel(LevelArgs a, uint32_t w) {
+__global__ void __launch_bounds__(kPermuteThreads, 4) permute_kernel(LevelArgs a, uint32_t w) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t units = a.B * w / (uint32_t)sizeof(U);
     const uint32_t tid = threadIdx.x;
@@ -521,6 +526,7 @@ __global__ void __launch_bounds__(kPermuteThreads) permute_kernel(LevelArgs a, u
     uint64_t chunk = ~0ull;   // current 64-slot chunk of start candidates
     uint32_t cpos = 64;       // next candidate inside the chunk
     uint32_t cw[8];           // the chunk's words, 8 per lane of the group (lane lg holds slots lg*8 ..)
+    uint32_t steps = 0;       // swaps of the current chain
 
     for (;;) {
         if (!carrying) {
@@ -578,6 +584,7 @@ __global__ void __launch_bounds__(kPermuteThreads) permute_kernel(LevelArgs a, u
             }
             carrying = true;
             dw = w0;
+            steps = 0;
             continue;
         }
 
@@ -611,9 +618,34 @@ __global__ void __launch_bounds__(kPermuteThreads) permute_kernel(LevelArgs a, u
             carrying = false;
             continue;
         }
-        U y[4];
+        if (steps >= a.park_after) {
+            // long chain: put the block aside (the destination keeps its unmoved block,
+            // which a chain start will read out later); placed after this kernel
+            uint32_t ok = 0;
+            uint64_t off = 0;
+            if (leader) {
+                const uint32_t rec = atomicAdd(&a.counters[6], 1u);
+                if (rec < a.park_cap) {
+                    const uint64_t alloc = ((uint64_t)a.B + a.pool_align - 1) / a.pool_align * a.pool_align;
+                    off = atomicAdd((unsigned long long*)a.pool_used, (unsigned long long)alloc);
+                    ok = off + a.B <= a.pool_cap && ((off * w) % sizeof(U)) == 0;
+                    a.parks[rec] = ParkRec{ok ? off : ~0ull, reinterpret_cast<uint64_t>(dp)};
+                }
+            }
+            ok = __shfl_sync(gmask, ok, leader_lane);
+            if (ok) {
+                off = __shfl_sync(gmask, off, leader_lane);
+                U* dst = reinterpret_cast<U*>(a.pool + off * w);
+                for (uint32_t u = lg; u < units; u += kGroup) dst[u] = buf[u];
+                __syncwarp(gmask);
+                carrying = false;
+                continue;
+            }
+            steps = 0x80000000u;  // no room: finish this chain without parking
+        }
+        U y[2];
 #pragma unroll
-        for (uint32_t j = 0; j < 4; ++j) {
+        for (uint32_t j = 0; j < 2; ++j) {
             const uint32_t u = lg + j * kGroup;
             if (u < units) y[j] = ld_cg(dp + u);
         }
@@ -644,20 +676,21 @@ __global__ void __launch_bounds__(kPermuteThreads) permute_kernel(LevelArgs a, u
         if (old & kWordOcc) {
             // swap: read the block at d, write ours, carry the one read
 #pragma unroll
-            for (uint32_t j = 0; j < 4; ++j) {
+            for (uint32_t j = 0; j < 2; ++j) {
                 const uint32_t u = lg + j * kGroup;
                 if (u < units) {
                     dp[u] = buf[u];
                     buf[u] = y[j];
                 }
             }
-            for (uint32_t u = lg + 4 * kGroup; u < units; u += kGroup) {
+            for (uint32_t u = lg + 2 * kGroup; u < units; u += kGroup) {
                 const U t = ld_cg(dp + u);
                 dp[u] = buf[u];
                 buf[u] = t;
             }
             __syncwarp(gmask);
             dw = old;
+            ++steps;
         } else {
             for (uint32_t u = lg; u < units; u += kGroup) dp[u] = buf[u];
             __syncwarp(gmask);
@@ -708,6 +741,24 @@ __global__ void tails_kernel(LevelArgs a) {
             }
         }
         __syncthreads();
+    }
+}
+
+// Parked blocks go to their destination slots, all of which were read out by
+// the permutation kernel.
+template <typename U>
+__global__ void parked_kernel(LevelArgs a, uint32_t w) {
+    const uint32_t n = min(a.counters[6], a.park_cap);
+    const uint32_t units = a.B * w / (uint32_t)sizeof(U);
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = gw; i < n; i += nw) {
+        const ParkRec r = a.parks[i];
+        if (r.pool_off == ~0ull) continue;
+        const U* src = reinterpret_cast<const U*>(a.pool + r.pool_off * w);
+        U* dst = reinterpret_cast<U*>(r.dst);
+        for (uint32_t u = lane; u < units; u += 32u) dst[u] = src[u];
     }
 }
 
@@ -838,6 +889,13 @@ static cudaError_t launch_level_w(const LevelArgs& a, uint32_t num_sms, cudaStre
         permute_kernel<T><<<num_sms * 8, kPermuteThreads, psm, s>>>(a, W);
     }
     {
+        ProfScope p("parked", s);
+        if (a.vec16)
+            parked_kernel<uint4><<<num_sms * 2, 256, 0, s>>>(a, W);
+        else
+            parked_kernel<typename Elem<W>::T><<<num_sms * 2, 256, 0, s>>>(a, W);
+    }
+    {
         ProfScope p("tails", s);
         tails_kernel<W><<<num_sms * 4, 512, 0, s>>>(a);
     }
@@ -845,7 +903,7 @@ static cudaError_t launch_level_w(const LevelArgs& a, uint32_t num_sms, cudaStre
         ProfScope p("demoted", s);
         demoted_kernel<W><<<num_sms, 256, 0, s>>>(a);
     }
-    if (launches) *launches += 7;
+    if (launches) *launches += 8;
     return cudaGetLastError();
 }
 

@@ -84,6 +84,7 @@ __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint3
     const uint64_t T64 = plan.T[li];
     const uint32_t T = T64 >= len ? len : (uint32_t)T64;
     const uint32_t tiles = (len + T - 1) / T;
+    const FastDiv fdT = FastDiv::make(T), fdB = FastDiv::make(B);
     const uint32_t ncnt = tiles * k;
     uint16_t* X = buf ? P1 : P0;
     uint16_t* Y = buf ? P0 : P1;
@@ -108,7 +109,7 @@ __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint3
                 const uint32_t v = gb + 32u * st + lane;
                 const bool valid = v >= delta && v - delta < len;
                 const uint32_t b = bucket_of(group_step_word(rr, st), k);
-                const uint32_t key2 = valid ? ((v - delta) / T) * k + b : 0xffffffffu;
+                const uint32_t key2 = valid ? (tiles == 1 ? 0u : fdT.div(v - delta)) * k + b : 0xffffffffu;
                 const uint32_t peers = __match_any_sync(0xffffffffu, key2);
                 if (valid && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&sh.thr[key2], (uint32_t)__popc(peers));
             }
@@ -136,16 +137,17 @@ __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint3
     for (uint32_t b = tid; b < k; b += blockDim.x) {
         const uint32_t sb = sh.run[b];
         uint32_t Fb = 0;
-        for (uint32_t t = 0; t < tiles; ++t) Fb += sh.thr[t * k + b] / B;
+        for (uint32_t t = 0; t < tiles; ++t) Fb += fdB.div(sh.thr[t * k + b]);
         uint32_t fsum = 0, rsum = 0;
         for (uint32_t t = 0; t < tiles; ++t) {
             const uint32_t c = sh.thr[t * k + b];
-            const uint32_t th = c - c % B;
+            const uint32_t f = fdB.div(c);
+            const uint32_t th = f * B;
             sh.fb[t * k + b] = sb + B * fsum;
             sh.tb[t * k + b] = sb + B * Fb + rsum - th;
             sh.thr[t * k + b] = th;
-            fsum += c / B;
-            rsum += c % B;
+            fsum += f;
+            rsum += c - th;
         }
     }
     __syncthreads();

@@ -154,3 +154,27 @@ def test_caller_workspace_allocates_nothing_else():
     small = torch.empty(max(need // 2, 256), dtype=torch.uint8, device="cuda")
     with pytest.raises(rip.RipError):
         rip.shuffle_(t, 21, plan=plan, ws=small)
+
+
+@pytest.mark.parametrize("park_after", [1, 3])
+def test_parked_chains(park_after):
+    """Chains put their block aside after a few steps (RIP_PARK_AFTER); the
+    parked blocks are placed afterwards: same output as the oracle."""
+    import os
+    import subprocess
+    import sys
+    code = (
+        "import numpy as np, torch, oracle, paper_2302_03317_gb300 as rip\n"
+        "for n, w, ks, Ts, Bs in [(1 << 21, 8, [16], [65536], [64]), (600_000, 4, [8, 4], [3000, 3 << 18], [6, 3])]:\n"
+        "    a = np.arange(n, dtype=np.uint64 if w == 8 else np.uint32)\n"
+        "    t = torch.from_numpy(a.view(np.int64) if w == 8 else a.view(np.int32)).cuda()\n"
+        "    p = rip.Plan(ks=ks, Ts=Ts, Bs=Bs, base=100)\n"
+        "    rip.shuffle_(t, 77, plan=p, check=True)\n"
+        "    got = t.cpu().numpy().view(a.dtype)\n"
+        "    want = oracle.shuffle(a, 77, oracle.Plan(ks, Ts, Bs, 100, 0))\n"
+        "    assert np.array_equal(got, want), (n, w)\n"
+        "print('ok')\n")
+    env = dict(os.environ, RIP_PARK_AFTER=str(park_after))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout[-2000:] + r.stderr[-4000:]
