@@ -31,9 +31,11 @@ namespace {
 
 // ------------------------------------------------------------------ helpers
 
-__device__ __forceinline__ uint32_t atom_or_acqrel(uint32_t* p, uint32_t v) {
+// Acquire: a slot read out by a chain start (release store of 0) may be written
+// only after that read; nothing written before this atomic needs ordering.
+__device__ __forceinline__ uint32_t atom_or_acquire(uint32_t* p, uint32_t v) {
     uint32_t old;
-    asm volatile("atom.acq_rel.gpu.global.or.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    asm volatile("atom.acquire.gpu.global.or.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
     return old;
 }
 
@@ -148,7 +150,7 @@ struct ClsShared {
     uint32_t binfo[kMaxK];    // per bucket this round: (run mod B) | (blocks completing) << 16
     uint32_t dfirst[kMaxK];   // first home index that is demoted, per bucket (this round)
     uint64_t dbase[kMaxK];    // pool offset of that demoted block
-    uint16_t tbl[kClsTbl];    // (ranking warp, bucket) counts of the round
+    uint32_t tbl[kClsTbl];    // (ranking warp, bucket) counts of the round
     uint16_t flist[kMaxK];    // buckets whose buffered block completes this round
     uint32_t scan[32];
     uint32_t nflush;
@@ -247,11 +249,11 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                     const uint32_t b = bucket_of(group_step_word(words[e / 4], e % 4), k);
                     const uint32_t kk = valid ? b : 0xffffffffu;
                     const uint32_t peers = __match_any_sync(0xffffffffu, kk);
-                    const uint32_t pre = valid ? sh.tbl[warp * k + b] : 0u;
-                    __syncwarp();
-                    if (valid && lane == (uint32_t)(__ffs(peers) - 1))
-                        sh.tbl[warp * k + b] = (uint16_t)(pre + __popc(peers));
-                    __syncwarp();
+                    const uint32_t leader = (uint32_t)(__ffs(peers) - 1);
+                    uint32_t pre = 0;
+                    // only this warp touches row `warp`: the returned count is the one before this step
+                    if (valid && lane == leader) pre = atomicAdd(&sh.tbl[warp * k + b], (uint32_t)__popc(peers));
+                    pre = __shfl_sync(0xffffffffu, pre, (int)leader);
                     bb[e] = valid ? b : 0xffffffffu;
                     rk[e] = pre + __popc(peers & lt_mask);
                 }
@@ -264,7 +266,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                 uint32_t tot = 0;
                 for (uint32_t w = 0; w < nwr; ++w) {
                     const uint32_t c = sh.tbl[w * k + b];
-                    sh.tbl[w * k + b] = (uint16_t)tot;
+                    sh.tbl[w * k + b] = tot;
                     tot += c;
                 }
                 const uint32_t rb = sh.run[b], nr = rb + tot;
@@ -508,7 +510,7 @@ __global__ void resolve_kernel(LevelArgs a) {
 // ------------------------------------------------------------------ permute
 
 template <typename U>
-__global__ void __launch_bounds__(kPermuteThreads, 4) permute_kernel(LevelArgs a, uint32_t w) {
+__global__ void __launch_bounds__(kPermuteThreads) permute_kernel(LevelArgs a, uint32_t w) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t units = a.B * w / (uint32_t)sizeof(U);
     const uint32_t tid = threadIdx.x;
@@ -577,11 +579,8 @@ __global__ void __launch_bounds__(kPermuteThreads, 4) permute_kernel(LevelArgs a
                 continue;
             }
             for (uint32_t u = lg; u < units; u += kGroup) buf[u] = ld_cg(sp + u);
-            __syncwarp(gmask);
-            if (leader) {
-                __threadfence();
-                st_release(&a.words[s], 0u);
-            }
+            __syncwarp(gmask);  // every lane's read of slot s has returned
+            if (leader) st_release(&a.words[s], 0u);
             carrying = true;
             dw = w0;
             steps = 0;
@@ -643,14 +642,14 @@ __global__ void __launch_bounds__(kPermuteThreads, 4) permute_kernel(LevelArgs a
             }
             steps = 0x80000000u;  // no room: finish this chain without parking
         }
-        U y[2];
+        U y[4];
 #pragma unroll
-        for (uint32_t j = 0; j < 2; ++j) {
+        for (uint32_t j = 0; j < 4; ++j) {
             const uint32_t u = lg + j * kGroup;
             if (u < units) y[j] = ld_cg(dp + u);
         }
         uint32_t old = 0;
-        if (leader) old = atom_or_acqrel(&a.words[d], kWordTaken);
+        if (leader) old = atom_or_acquire(&a.words[d], kWordTaken);
         old = __shfl_sync(gmask, old, leader_lane);
         __syncwarp(gmask);  // order the group's accesses to d after the leader's acquire
         if (old & kWordTaken) {
@@ -676,14 +675,14 @@ __global__ void __launch_bounds__(kPermuteThreads, 4) permute_kernel(LevelArgs a
         if (old & kWordOcc) {
             // swap: read the block at d, write ours, carry the one read
 #pragma unroll
-            for (uint32_t j = 0; j < 2; ++j) {
+            for (uint32_t j = 0; j < 4; ++j) {
                 const uint32_t u = lg + j * kGroup;
                 if (u < units) {
                     dp[u] = buf[u];
                     buf[u] = y[j];
                 }
             }
-            for (uint32_t u = lg + 2 * kGroup; u < units; u += kGroup) {
+            for (uint32_t u = lg + 4 * kGroup; u < units; u += kGroup) {
                 const U t = ld_cg(dp + u);
                 dp[u] = buf[u];
                 buf[u] = t;

@@ -19,12 +19,23 @@ constexpr uint32_t kThreads = kSmallThreads;
 constexpr uint32_t kWarps = kThreads / 32;
 constexpr uint32_t kE = 4;  // 32-element steps per ranking warp per round
 
-struct SmallShared {
+struct GeneralScratch {         // scatter of a range with several tiles or k > 256
     uint32_t thr[kSmallCntCap];  // per (tile, bucket): count, then B*floor(count/B)
     uint32_t fb[kSmallCntCap];   // per (tile, bucket): first full-block destination
     uint32_t tb[kSmallCntCap];   // per (tile, bucket): tail destination minus thr
     uint32_t run[kMaxK];         // per bucket: elements seen so far in the current tile
-    uint16_t tbl[kSmallTbl];     // per (ranking warp, bucket): running count in a round
+    uint32_t tbl[kSmallTbl / 2]; // per (ranking warp, bucket): running count in a round
+};
+struct FastScratch {             // single-tile scatter with k <= 256
+    uint32_t hist[kWarps * 256]; // per (warp, bucket): count, then first output index
+    uint32_t start[256];         // per bucket: total, then first output index of the bucket
+};
+
+struct SmallShared {
+    union {
+        GeneralScratch g;
+        FastScratch f;
+    };
     uint64_t stack[kSmallStack]; // pending scatter ranges
     uint32_t scan[32];
     uint32_t stack_top;
@@ -73,6 +84,136 @@ __device__ void fy_block(uint16_t* Z, uint16_t* draws, uint32_t len, PhiloxKey k
     __syncthreads();
 }
 
+// Children of a scattered range: leaves are finished right away, larger ones
+// are pushed for another scatter.  start(b) = first output index of bucket b.
+template <typename StartFn>
+__device__ void finish_children(SmallShared& sh, uint16_t* P0, uint16_t* Y, uint32_t a, uint32_t len, uint32_t k,
+                                uint32_t L, uint32_t buf, const DevPlan& plan, PhiloxKey key, uint64_t o_r,
+                                Status* status, StartFn start) {
+    for (uint32_t b = threadIdx.x; b < k; b += blockDim.x) {
+        const uint32_t sb = start(b);
+        const uint32_t se = b + 1 < k ? start(b + 1) : len;
+        const uint32_t size = se - sb;
+        if (size == 0) continue;
+        if (se > len || sb > se) {
+            report(status, RIP_EINTERNAL, 0x5104, se);
+            continue;
+        }
+        if (size == 1 || plan.is_leaf(size, L + 1)) {
+            uint16_t* Z = Y + a + sb;
+            if (size > 1) fy_serial(Z, size, key, L + 1, o_r + sb);
+            if (Y != P0)
+                for (uint32_t j = 0; j < size; ++j) P0[a + sb + j] = Z[j];
+        } else {
+            const uint32_t slot = atomicAdd(&sh.stack_top, 1u);
+            if (slot < kSmallStack)
+                sh.stack[slot] = pack_range(a + sb, size, L + 1, buf ^ 1u);
+            else
+                report(status, RIP_EINTERNAL, 0x5102, slot);
+        }
+    }
+    __syncthreads();
+}
+
+// Scatter of a range that is a single tile with k <= 256: a stable partition
+// by bucket.  Warp w owns a contiguous run of 128-position groups (aligned to
+// multiples of four in the global position space).  Pass 1: each lane draws
+// the four buckets of one Philox call per group (kept packed in registers) and
+// counts them in the warp's histogram row.  Prefix: rows become the first
+// output index of (warp, bucket).  Pass 2: the warp walks its run in position
+// order, 32 positions per step; match_any gives the rank inside the step and
+// one shared atomic per bucket and step advances the warp's row.
+constexpr uint32_t kFastGroups = 24;  // groups per warp: 16 warps x 24 x 128 >= 48K + 3
+
+__device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint32_t a, uint32_t len, uint32_t L,
+                                   uint32_t buf, const DevPlan& plan, PhiloxKey key, uint64_t sub_o, Status* status) {
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t k = plan.k[plan.idx(L)];
+    uint16_t* X = buf ? P1 : P0;
+    uint16_t* Y = buf ? P0 : P1;
+    const uint64_t o_r = sub_o + a;
+    const uint32_t delta = (uint32_t)(o_r & 3u);
+    const uint64_t Q0 = o_r >> 2;
+    const uint32_t ngroups = (len + delta + 127u) / 128u;
+    const uint32_t gpw = (ngroups + kWarps - 1) / kWarps;  // groups per warp (<= kFastGroups)
+    const uint32_t g0 = warp * gpw;
+    uint32_t* hist = sh.f.hist;
+    for (uint32_t j = tid; j < kWarps * k; j += blockDim.x) hist[j] = 0;
+    __syncthreads();
+
+    uint32_t bk[kFastGroups];  // 4 packed 8-bit buckets per group: lane l holds positions 4l .. 4l+3
+#pragma unroll
+    for (uint32_t g = 0; g < kFastGroups; ++g) {
+        bk[g] = 0;
+        if (g < gpw && g0 + g < ngroups) {
+            const uint32_t vg = (g0 + g) * 128u;
+            const uint4 r = group_philox(key, L, o_r, Q0 + vg / 4u);
+            const uint32_t v0 = vg + 4u * lane;
+            const uint32_t w4[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+            for (uint32_t j = 0; j < 4; ++j) {
+                const uint32_t b = bucket_of(w4[j], k);
+                bk[g] |= b << (8 * j);
+                const uint32_t v = v0 + j;
+                if (v >= delta && v - delta < len) atomicAdd(&hist[warp * k + b], 1u);
+            }
+        }
+    }
+    __syncthreads();
+    // rows -> first output index of (warp, bucket)
+    for (uint32_t b = tid; b < k; b += blockDim.x) {
+        uint32_t acc = 0;
+        for (uint32_t w = 0; w < kWarps; ++w) {
+            const uint32_t c = hist[w * k + b];
+            hist[w * k + b] = acc;
+            acc += c;
+        }
+        sh.f.start[b] = acc;  // bucket total
+    }
+    __syncthreads();
+    {
+        const uint32_t i0 = 2 * tid, i1 = 2 * tid + 1;
+        const uint32_t v0 = i0 < k ? sh.f.start[i0] : 0, v1 = i1 < k ? sh.f.start[i1] : 0;
+        const uint32_t ex = block_exclusive_scan<uint32_t>(v0 + v1, sh.scan, nullptr);
+        if (i0 < k) sh.f.start[i0] = ex;
+        if (i1 < k) sh.f.start[i1] = ex + v0;
+    }
+    __syncthreads();
+    for (uint32_t j = tid; j < kWarps * k; j += blockDim.x) hist[j] += sh.f.start[j & (k - 1u)];  // k is a power of two
+    __syncthreads();
+
+    const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+    for (uint32_t g = 0; g < kFastGroups; ++g) {
+        if (g < gpw && g0 + g < ngroups) {
+            const uint32_t vg = (g0 + g) * 128u;
+#pragma unroll
+            for (uint32_t st = 0; st < 4; ++st) {
+                const uint32_t packed = __shfl_sync(0xffffffffu, bk[g], (int)(8u * st + (lane >> 2)));
+                const uint32_t b = (packed >> (8u * (lane & 3u))) & 0xFFu;
+                const uint32_t v = vg + 32u * st + lane;
+                const bool valid = v >= delta && v - delta < len;
+                const uint32_t kk = valid ? b : 0xffffffffu;
+                const uint32_t peers = __match_any_sync(0xffffffffu, kk);
+                const uint32_t leader = (uint32_t)(__ffs(peers) - 1);
+                uint32_t base = 0;
+                if (valid && lane == leader) base = atomicAdd(&hist[warp * k + b], (uint32_t)__popc(peers));
+                base = __shfl_sync(0xffffffffu, base, (int)leader);
+                if (valid) {
+                    const uint32_t d = base + __popc(peers & lt_mask);
+                    if (d < len) Y[a + d] = X[a + (v - delta)];
+                    else report(status, RIP_EINTERNAL, 0x5105, d);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // bucket starts survive in sh.f.start[0..k)
+    finish_children(sh, P0, Y, a, len, k, L, buf, plan, key, o_r, status,
+                    [&](uint32_t b) { return sh.f.start[b]; });
+    return true;
+}
+
 // One scatter level of the range [a, a+len) (level L) from X into Y, both
 // index arrays; children ranges are finished (leaves) or pushed.
 __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint32_t a, uint32_t len,
@@ -94,7 +235,11 @@ __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint3
         if (tid == 0) report(status, RIP_EINTERNAL, 0x5101, ncnt);
         return;
     }
-    for (uint32_t j = tid; j < ncnt; j += blockDim.x) sh.thr[j] = 0;
+    if (tiles == 1 && k <= 256 && (len + 3u + 127u) / 128u <= kWarps * kFastGroups) {
+        scatter_range_fast(sh, P0, P1, a, len, L, buf, plan, key, sub_o, status);
+        return;
+    }
+    for (uint32_t j = tid; j < ncnt; j += blockDim.x) sh.g.thr[j] = 0;
     __syncthreads();
 
     // counts per (tile, bucket); groups of 128 positions aligned to multiples of four
@@ -111,7 +256,7 @@ __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint3
                 const uint32_t b = bucket_of(group_step_word(rr, st), k);
                 const uint32_t key2 = valid ? (tiles == 1 ? 0u : fdT.div(v - delta)) * k + b : 0xffffffffu;
                 const uint32_t peers = __match_any_sync(0xffffffffu, key2);
-                if (valid && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&sh.thr[key2], (uint32_t)__popc(peers));
+                if (valid && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&sh.g.thr[key2], (uint32_t)__popc(peers));
             }
         }
     }
@@ -120,32 +265,32 @@ __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint3
     // bucket sizes -> region starts s_b (exclusive scan over b)
     for (uint32_t b = tid; b < k; b += blockDim.x) {
         uint32_t size = 0;
-        for (uint32_t t = 0; t < tiles; ++t) size += sh.thr[t * k + b];
-        sh.run[b] = size;
+        for (uint32_t t = 0; t < tiles; ++t) size += sh.g.thr[t * k + b];
+        sh.g.run[b] = size;
     }
     __syncthreads();
     {
         // k <= kMaxK = 1024 = 2 * kThreads: two entries per thread
         const uint32_t i0 = 2 * tid, i1 = 2 * tid + 1;
-        const uint32_t v0 = i0 < k ? sh.run[i0] : 0, v1 = i1 < k ? sh.run[i1] : 0;
+        const uint32_t v0 = i0 < k ? sh.g.run[i0] : 0, v1 = i1 < k ? sh.g.run[i1] : 0;
         const uint32_t ex = block_exclusive_scan<uint32_t>(v0 + v1, sh.scan, nullptr);
-        if (i0 < k) sh.run[i0] = ex;
-        if (i1 < k) sh.run[i1] = ex + v0;
+        if (i0 < k) sh.g.run[i0] = ex;
+        if (i1 < k) sh.g.run[i1] = ex + v0;
     }
     __syncthreads();
     // per (tile, bucket): full-block and tail destinations of the canonical layout
     for (uint32_t b = tid; b < k; b += blockDim.x) {
-        const uint32_t sb = sh.run[b];
+        const uint32_t sb = sh.g.run[b];
         uint32_t Fb = 0;
-        for (uint32_t t = 0; t < tiles; ++t) Fb += fdB.div(sh.thr[t * k + b]);
+        for (uint32_t t = 0; t < tiles; ++t) Fb += fdB.div(sh.g.thr[t * k + b]);
         uint32_t fsum = 0, rsum = 0;
         for (uint32_t t = 0; t < tiles; ++t) {
-            const uint32_t c = sh.thr[t * k + b];
+            const uint32_t c = sh.g.thr[t * k + b];
             const uint32_t f = fdB.div(c);
             const uint32_t th = f * B;
-            sh.fb[t * k + b] = sb + B * fsum;
-            sh.tb[t * k + b] = sb + B * Fb + rsum - th;
-            sh.thr[t * k + b] = th;
+            sh.g.fb[t * k + b] = sb + B * fsum;
+            sh.g.tb[t * k + b] = sb + B * Fb + rsum - th;
+            sh.g.thr[t * k + b] = th;
             fsum += f;
             rsum += c - th;
         }
@@ -155,7 +300,7 @@ __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint3
     // stable ranks inside each (tile, bucket), then the move X -> Y.  A round covers
     // nwr groups of 128 positions; tbl[w][b] counts bucket b in warp w's group, then
     // holds the element rank base (running count of the tile + earlier warps).
-    const uint32_t nwr = min(kWarps, (uint32_t)kSmallTbl / k);
+    const uint32_t nwr = min(kWarps, (uint32_t)(kSmallTbl / 2) / k);
     const uint32_t round = nwr * 128u;
     const uint32_t lt_mask = (1u << lane) - 1u;
     for (uint32_t t = 0; t < tiles; ++t) {
@@ -164,8 +309,8 @@ __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint3
         const uint32_t delta = (uint32_t)(P0 & 3u);
         const uint64_t Q0 = P0 >> 2;
         const uint32_t tl = hi - lo, vlen = tl + delta;
-        for (uint32_t b = tid; b < k; b += blockDim.x) sh.run[b] = 0;
-        for (uint32_t j = tid; j < nwr * k; j += blockDim.x) sh.tbl[j] = 0;
+        for (uint32_t b = tid; b < k; b += blockDim.x) sh.g.run[b] = 0;
+        for (uint32_t j = tid; j < nwr * k; j += blockDim.x) sh.g.tbl[j] = 0;
         __syncthreads();
         for (uint32_t R = 0; R < vlen; R += round) {
             uint32_t bb[4], pr[4];
@@ -178,11 +323,10 @@ __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint3
                     const uint32_t b = bucket_of(group_step_word(rr, st), k);
                     const uint32_t kk = valid ? b : 0xffffffffu;
                     const uint32_t peers = __match_any_sync(0xffffffffu, kk);
-                    const uint32_t pre = valid ? sh.tbl[warp * k + b] : 0u;
-                    __syncwarp();
-                    if (valid && lane == (uint32_t)(__ffs(peers) - 1))
-                        sh.tbl[warp * k + b] = (uint16_t)(pre + __popc(peers));
-                    __syncwarp();
+                    const uint32_t leader = (uint32_t)(__ffs(peers) - 1);
+                    uint32_t pre = 0;
+                    if (valid && lane == leader) pre = atomicAdd(&sh.g.tbl[warp * k + b], (uint32_t)__popc(peers));
+                    pre = __shfl_sync(0xffffffffu, pre, (int)leader);
                     bb[st] = valid ? b : 0xffffffffu;
                     pr[st] = pre + __popc(peers & lt_mask);
                 }
@@ -190,13 +334,13 @@ __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint3
             __syncthreads();
             // rank bases: running count of the tile plus the counts of earlier warps
             for (uint32_t b = tid; b < k; b += blockDim.x) {
-                uint32_t acc = sh.run[b];
+                uint32_t acc = sh.g.run[b];
                 for (uint32_t w = 0; w < nwr; ++w) {
-                    const uint32_t c = sh.tbl[w * k + b];
-                    sh.tbl[w * k + b] = (uint16_t)acc;
+                    const uint32_t c = sh.g.tbl[w * k + b];
+                    sh.g.tbl[w * k + b] = acc;
                     acc += c;
                 }
-                sh.run[b] = acc;
+                sh.g.run[b] = acc;
             }
             __syncthreads();
             if (warp < nwr) {
@@ -204,9 +348,9 @@ __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint3
                 for (uint32_t st = 0; st < 4; ++st) {
                     const uint32_t b = bb[st];
                     if (b == 0xffffffffu) continue;
-                    const uint32_t rank = sh.tbl[warp * k + b] + pr[st];
+                    const uint32_t rank = sh.g.tbl[warp * k + b] + pr[st];
                     const uint32_t ci = t * k + b;
-                    const uint32_t d = rank < sh.thr[ci] ? sh.fb[ci] + rank : sh.tb[ci] + rank;
+                    const uint32_t d = rank < sh.g.thr[ci] ? sh.g.fb[ci] + rank : sh.g.tb[ci] + rank;
                     const uint32_t i = lo + (R + warp * 128u + 32u * st + lane - delta);
                     if (d >= len) {  // cannot happen for consistent counts; never write out of range
                         report(status, RIP_EINTERNAL, 0x5103, d);
@@ -216,37 +360,15 @@ __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint3
                 }
                 __syncwarp();
                 // each warp reads only its own row: clear it for the next round
-                for (uint32_t b = lane; b < k; b += 32u) sh.tbl[warp * k + b] = 0;
+                for (uint32_t b = lane; b < k; b += 32u) sh.g.tbl[warp * k + b] = 0;
                 __syncwarp();
             }
         }
         __syncthreads();
     }
 
-    // children: leaves now, larger ones onto the stack
-    for (uint32_t b = tid; b < k; b += blockDim.x) {
-        const uint32_t sb = sh.fb[b];  // tile 0 entry = s_b
-        const uint32_t se = b + 1 < k ? sh.fb[b + 1] : len;
-        const uint32_t size = se - sb;
-        if (size == 0) continue;
-        if (se > len || sb > se) {
-            report(status, RIP_EINTERNAL, 0x5104, se);
-            continue;
-        }
-        if (size == 1 || plan.is_leaf(size, L + 1)) {
-            uint16_t* Z = Y + a + sb;
-            if (size > 1) fy_serial(Z, size, key, L + 1, o_r + sb);
-            if (Y != P0)
-                for (uint32_t j = 0; j < size; ++j) P0[a + sb + j] = Z[j];
-        } else {
-            const uint32_t slot = atomicAdd(&sh.stack_top, 1u);
-            if (slot < kSmallStack)
-                sh.stack[slot] = pack_range(a + sb, size, L + 1, buf ^ 1u);
-            else
-                report(status, RIP_EINTERNAL, 0x5102, slot);
-        }
-    }
-    __syncthreads();
+    // children: leaves now, larger ones onto the stack (tile 0 entry of fb = s_b)
+    finish_children(sh, P0, Y, a, len, k, L, buf, plan, key, o_r, status, [&](uint32_t b) { return sh.g.fb[b]; });
 }
 
 template <int W>

@@ -178,3 +178,12 @@ def test_parked_chains(park_after):
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     r = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0 and "ok" in r.stdout, r.stdout[-2000:] + r.stderr[-4000:]
+
+
+@pytest.mark.parametrize("n,w,plan", [
+    (300_000, 4, rip.Plan(ks=[32], Ts=[7000], Bs=[7], base=200)),
+    (200_000, 8, rip.Plan(ks=[16], Ts=[4096], Bs=[1], base=300)),
+    (250_000, 16, rip.Plan(ks=[8, 8], Ts=[4095, 4095], Bs=[45, 15], base=64)),
+])
+def test_odd_block_sizes(n, w, plan):
+    check(n, w, plan, seed=31)
