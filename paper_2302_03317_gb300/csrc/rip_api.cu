@@ -290,7 +290,11 @@ Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& 
     L.dem = take(sizeof(DemRec) * L.dem_cap);
     L.park_cap = L.levels ? (uint32_t)std::min<uint64_t>(65536, slots / 16 + 64) : 0;
     L.parks = take(sizeof(ParkRec) * L.park_cap);
-    L.mscratch = take((size_t)kMediumGrid * kMediumMaxM * w);
+    // the medium solver (data in global scratch) runs only for subproblems above the
+    // shared-memory limit: children of in-place levels, or a root in that range
+    bool need_medium = L.levels > 0;
+    for (uint64_t n : ns) need_medium |= n > L.small_max_m && n <= kMediumMaxM;
+    L.mscratch = take(need_medium ? (size_t)kMediumGrid * kMediumMaxM * w : 0);
     L.total = off;
     (void)meta_start;
     L.aux_bytes = off;
