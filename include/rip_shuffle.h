@@ -57,7 +57,8 @@ enum {
     RIP_EWORKSPACE = 3, /* caller workspace too small / device pool exhausted */
     RIP_ECUDA = 4,      /* a CUDA runtime call failed                         */
     RIP_ETIMEOUT = 5,   /* a bounded device-side wait expired                 */
-    RIP_EINTERNAL = 6   /* a device-side consistency check failed            */
+    RIP_EINTERNAL = 6,  /* a device-side consistency check failed            */
+    RIP_ETOOLARGE = 7   /* input needs more than rip_shuffle_noalloc's fixed workspace */
 };
 
 #define RIP_MAX_LEVEL_PARAMS 8
@@ -138,6 +139,26 @@ const char *rip_strerror(int code);
  *   out[2] kernels launched by the call.
  * Returns RIP_EINVAL if out is NULL. */
 int rip_last_call_info(uint64_t out[3]);
+
+/* Allocation-free variant of rip_shuffle_ex (the paper has no counterpart: it
+ * is an interface for callers that must not allocate device memory, such as
+ * code running inside a framework's own allocator or memory pool, processes
+ * whose device memory is reserved up front by a pool owner, or paths that
+ * cannot afford cudaMalloc's implicit synchronisation).  Its workspace is a
+ * fixed array of RIP_NOALLOC_WS_BYTES in the library's device image, which
+ * every GPU that loads the library holds until the process exits; the call
+ * performs no allocation.  Inputs whose workspace
+ * (rip_shuffle_workspace_size) exceeds the array are rejected with
+ * RIP_ETOOLARGE before anything is enqueued; with the default plan that is
+ * about 2^22 elements of 4 or 8 bytes or 2^20 16-byte records.  The first call
+ * on a device looks up the array's device address (a one-time set-up); make
+ * that first call before any stream capture.  All calls share the array and
+ * each call clears what must start at zero; calls that overlap on the GPU race
+ * on it and must be serialised by the caller.  Arguments and results as in
+ * rip_shuffle_ex without ws / ws_bytes. */
+#define RIP_NOALLOC_WS_BYTES (32u << 20)
+int rip_shuffle_noalloc(void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed,
+                        const rip_plan *plan, rip_stream_t stream);
 
 /* Kernel timing (the measurement side of the library, no counterpart in the
  * paper, which reports wall-clock means only, Sec. 6): while enabled, every

@@ -20,7 +20,7 @@ from . import build as _build
 _lock = threading.Lock()
 _lib = None
 
-RIP_OK, RIP_EINVAL, RIP_ENOMEM, RIP_EWORKSPACE, RIP_ECUDA, RIP_ETIMEOUT, RIP_EINTERNAL = range(7)
+RIP_OK, RIP_EINVAL, RIP_ENOMEM, RIP_EWORKSPACE, RIP_ECUDA, RIP_ETIMEOUT, RIP_EINTERNAL, RIP_ETOOLARGE = range(8)
 RIP_MAX_LEVEL_PARAMS = 8
 
 
@@ -110,6 +110,8 @@ def _load():
         lib.rip_strerror.restype = ctypes.c_char_p
         lib.rip_last_call_info.argtypes = [ctypes.POINTER(u64)]
         lib.rip_last_call_info.restype = i32
+        lib.rip_shuffle_noalloc.argtypes = [vp, u64, u32, u64, pplan, vp]
+        lib.rip_shuffle_noalloc.restype = i32
         lib.rip_profile_enable.argtypes = [i32]
         lib.rip_profile_enable.restype = i32
         lib.rip_profile_reset.argtypes = []
@@ -153,6 +155,13 @@ def rip_shuffle_ex(data_ptr: int, n: int, elem_bytes: int, seed: int, plan=None,
                    ws_bytes: int = 0, stream: int = 0) -> None:
     _check(_load().rip_shuffle_ex(data_ptr, n, elem_bytes, seed, _plan_ptr(plan), ws_ptr or None, ws_bytes,
                                   stream), "rip_shuffle_ex")
+
+
+def rip_shuffle_noalloc(data_ptr: int, n: int, elem_bytes: int, seed: int, plan=None, stream: int = 0) -> None:
+    """The shuffle with the library's fixed device workspace: no allocation
+    (for callers that must not allocate device memory)."""
+    _check(_load().rip_shuffle_noalloc(data_ptr, n, elem_bytes, seed, _plan_ptr(plan), stream),
+           "rip_shuffle_noalloc")
 
 
 def rip_shuffle_batched_workspace_size(ns: Sequence[int], elem_bytes: int, plan=None) -> int:

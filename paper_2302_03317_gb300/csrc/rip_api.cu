@@ -647,6 +647,7 @@ const char* rip_strerror(int code) {
         case RIP_ECUDA: return "CUDA runtime error";
         case RIP_ETIMEOUT: return "device-side wait limit expired";
         case RIP_EINTERNAL: return "device-side consistency check failed";
+        case RIP_ETOOLARGE: return "input too large for the fixed workspace of rip_shuffle_noalloc";
         default: return "unknown error";
     }
 }
