@@ -117,6 +117,28 @@ __device__ __forceinline__ uint32_t group_step_word(const uint4& r, uint32_t s) 
 
 __device__ __forceinline__ uint32_t bucket_of(uint32_t word, uint32_t k) { return __umulhi(word, k); }
 
+// Lanes of the warp holding the same bucket as the calling lane (among lanes
+// with `valid`), from one ballot per bucket bit: cheaper than match.any when
+// most of the 32 buckets differ.  bits = log2 k <= 10; all lanes must call.
+__device__ __forceinline__ uint32_t warp_peers(uint32_t b, uint32_t bits, bool valid) {
+    uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+    for (uint32_t i = 0; i < 10; ++i) {
+        if (i < bits) {
+            const uint32_t bit = (b >> i) & 1u;
+            const uint32_t m = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? m : ~m;
+        }
+    }
+    return peers;
+}
+
+__host__ __device__ __forceinline__ uint32_t log2_pow2(uint32_t k) {
+    uint32_t l = 0;
+    while ((1u << l) < k) ++l;
+    return l;
+}
+
 // Lemire acceptance for s in [1, 2^32]: returns true and sets v on accept.
 __device__ __forceinline__ bool lemire_accept(uint32_t x, uint64_t s, uint64_t& v) {
     const uint64_t m = (uint64_t)x * s;

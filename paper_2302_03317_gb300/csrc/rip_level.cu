@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
     ClsShared& sh = *reinterpret_cast<ClsShared*>(smem_raw);
     T* buf = reinterpret_cast<T*>(smem_raw + ((sizeof(ClsShared) + 15) & ~size_t(15)));
     const uint32_t k = a.k, B = a.B, L = a.level;
+    const uint32_t kbits = log2_pow2(k);
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t nwarps = blockDim.x >> 5;
     const uint32_t nwr = min(nwarps, kClsTbl / k);
@@ -247,9 +248,8 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                     const uint32_t v = R + (warp * G + e / 4) * 128u + 32u * (e % 4) + lane;
                     const bool valid = v >= delta && v - delta < r;
                     const uint32_t b = bucket_of(group_step_word(words[e / 4], e % 4), k);
-                    const uint32_t kk = valid ? b : 0xffffffffu;
-                    const uint32_t peers = __match_any_sync(0xffffffffu, kk);
-                    const uint32_t leader = (uint32_t)(__ffs(peers) - 1);
+                    const uint32_t peers = warp_peers(b, kbits, valid);
+                    const uint32_t leader = valid ? (uint32_t)(__ffs(peers) - 1) : lane;
                     uint32_t pre = 0;
                     // only this warp touches row `warp`: the returned count is the one before this step
                     if (valid && lane == leader) pre = atomicAdd(&sh.tbl[warp * k + b], (uint32_t)__popc(peers));

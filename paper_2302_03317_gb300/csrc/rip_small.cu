@@ -16,8 +16,9 @@ namespace rip {
 namespace {
 
 constexpr uint32_t kThreads = kSmallThreads;
+// leaves up to this size use the parallel Fisher-Yates; its reservation words
+// live in the general scratch area (sizeof(GeneralScratch) / 4 words)
 constexpr uint32_t kWarps = kThreads / 32;
-constexpr uint32_t kE = 4;  // 32-element steps per ranking warp per round
 
 struct GeneralScratch {         // scatter of a range with several tiles or k > 256
     uint32_t thr[kSmallCntCap];  // per (tile, bucket): count, then B*floor(count/B)
@@ -30,6 +31,8 @@ struct FastScratch {             // single-tile scatter with k <= 256
     uint32_t hist[kWarps * 256]; // per (warp, bucket): count, then first output index
     uint32_t start[256];         // per bucket: total, then first output index of the bucket
 };
+
+constexpr uint32_t kParallelFyMax = (uint32_t)(sizeof(GeneralScratch) / sizeof(uint32_t));
 
 struct SmallShared {
     union {
@@ -57,6 +60,64 @@ __device__ void fy_serial(uint16_t* Z, uint32_t len, PhiloxKey key, uint32_t L, 
         Z[i] = Z[j];
         Z[j] = zi;
     }
+}
+
+// Partner draws H[i] (i >= 1) of a leaf, computed by the whole block.
+__device__ void fy_draws(uint16_t* H, uint32_t len, PhiloxKey key, uint32_t L, uint64_t leaf_o) {
+    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
+        if (i == 0) continue;
+        const uint64_t p = leaf_o + i;
+        const uint64_t q = p >> 2;
+        const uint4 r = philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), L | (kTagFy << 8), (uint32_t)leaf_o, key);
+        uint64_t v;
+        if (!lemire_accept(pick(r, (uint32_t)(p & 3u)), i + 1, v)) v = fy_draw_retry(key, L, leaf_o, p, i + 1);
+        H[i] = (uint16_t)v;
+    }
+    __syncthreads();
+}
+
+// Fisher-Yates over Z[0..len) in parallel with the same result as the sequential
+// loop for the same draws (deterministic reservations; Shun, Gu, Blelloch,
+// Fineman, Gibbons, SODA 2015, which the paper cites for parallel Fisher-Yates):
+// step i swaps positions i and H[i] <= i and must follow every larger step that
+// touches either position.  Each round, every unfinished step writes its index
+// into both positions' reservation word with atomicMax; a step holding both
+// reservations performs its swap.  H's top bit marks finished steps; len < 2^15.
+__device__ void fy_parallel(uint16_t* Z, uint16_t* H, uint32_t* R, uint32_t len, Status* status) {
+    __shared__ uint32_t remaining;
+    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) R[i] = 0;
+    if (threadIdx.x == 0) H[0] = 0x8000u;  // step 0 does nothing
+    for (uint32_t round = 0;; ++round) {
+        __syncthreads();
+        if (threadIdx.x == 0) remaining = 0;
+        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
+            const uint32_t h = H[i];
+            if (h & 0x8000u) continue;
+            atomicMax(&R[i], i);
+            atomicMax(&R[h], i);
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
+            const uint32_t h = H[i];
+            if (h & 0x8000u) continue;
+            if (R[i] == i && R[h] == i) {
+                const uint16_t zi = Z[i];
+                Z[i] = Z[h];
+                Z[h] = zi;
+                H[i] = (uint16_t)(h | 0x8000u);
+            } else {
+                remaining = 1;
+            }
+        }
+        __syncthreads();
+        if (!remaining) break;
+        if (round > 4 * len) {  // cannot happen: the largest unfinished step always commits
+            if (threadIdx.x == 0) report(status, RIP_EINTERNAL, 0x5106, len);
+            break;
+        }
+        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) R[i] = 0;
+    }
+    __syncthreads();
 }
 
 // Fisher-Yates over Z[0..len) with the partner draws computed by the whole
@@ -129,6 +190,7 @@ __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, 
                                    uint32_t buf, const DevPlan& plan, PhiloxKey key, uint64_t sub_o, Status* status) {
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t k = plan.k[plan.idx(L)];
+    const uint32_t kbits = log2_pow2(k);
     uint16_t* X = buf ? P1 : P0;
     uint16_t* Y = buf ? P0 : P1;
     const uint64_t o_r = sub_o + a;
@@ -193,9 +255,8 @@ __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, 
                 const uint32_t b = (packed >> (8u * (lane & 3u))) & 0xFFu;
                 const uint32_t v = vg + 32u * st + lane;
                 const bool valid = v >= delta && v - delta < len;
-                const uint32_t kk = valid ? b : 0xffffffffu;
-                const uint32_t peers = __match_any_sync(0xffffffffu, kk);
-                const uint32_t leader = (uint32_t)(__ffs(peers) - 1);
+                const uint32_t peers = warp_peers(b, kbits, valid);
+                const uint32_t leader = valid ? (uint32_t)(__ffs(peers) - 1) : lane;
                 uint32_t base = 0;
                 if (valid && lane == leader) base = atomicAdd(&hist[warp * k + b], (uint32_t)__popc(peers));
                 base = __shfl_sync(0xffffffffu, base, (int)leader);
@@ -226,6 +287,7 @@ __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint3
     const uint32_t T = T64 >= len ? len : (uint32_t)T64;
     const uint32_t tiles = (len + T - 1) / T;
     const FastDiv fdT = FastDiv::make(T), fdB = FastDiv::make(B);
+    const uint32_t kbits = log2_pow2(k);
     const uint32_t ncnt = tiles * k;
     uint16_t* X = buf ? P1 : P0;
     uint16_t* Y = buf ? P0 : P1;
@@ -254,9 +316,8 @@ __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint3
                 const uint32_t v = gb + 32u * st + lane;
                 const bool valid = v >= delta && v - delta < len;
                 const uint32_t b = bucket_of(group_step_word(rr, st), k);
-                const uint32_t key2 = valid ? (tiles == 1 ? 0u : fdT.div(v - delta)) * k + b : 0xffffffffu;
-                const uint32_t peers = __match_any_sync(0xffffffffu, key2);
-                if (valid && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&sh.g.thr[key2], (uint32_t)__popc(peers));
+                const uint32_t key2 = valid ? (tiles == 1 ? 0u : fdT.div(v - delta)) * k + b : 0u;
+                if (valid) atomicAdd(&sh.g.thr[key2], 1u);  // counts only: order does not matter
             }
         }
     }
@@ -321,9 +382,8 @@ __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint3
                     const uint32_t v = R + warp * 128u + 32u * st + lane;
                     const bool valid = v >= delta && v - delta < tl;
                     const uint32_t b = bucket_of(group_step_word(rr, st), k);
-                    const uint32_t kk = valid ? b : 0xffffffffu;
-                    const uint32_t peers = __match_any_sync(0xffffffffu, kk);
-                    const uint32_t leader = (uint32_t)(__ffs(peers) - 1);
+                    const uint32_t peers = warp_peers(b, kbits, valid);
+                    const uint32_t leader = valid ? (uint32_t)(__ffs(peers) - 1) : lane;
                     uint32_t pre = 0;
                     if (valid && lane == leader) pre = atomicAdd(&sh.g.tbl[warp * k + b], (uint32_t)__popc(peers));
                     pre = __shfl_sync(0xffffffffu, pre, (int)leader);
@@ -413,7 +473,12 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(SmallArgs args) {
         __syncthreads();
 
         if (plan.is_leaf(m, s.level)) {
-            if (m > 1) fy_block(P0, P1, m, key, s.level, s.o);
+            if (m > 1 && m <= kParallelFyMax) {
+                fy_draws(P1, m, key, s.level, s.o);
+                fy_parallel(P0, P1, sh.g.thr, m, args.status);
+            } else if (m > 1) {
+                fy_block(P0, P1, m, key, s.level, s.o);
+            }
         } else {
             if (tid == 0) {
                 sh.stack[0] = pack_range(0, m, s.level, 0);
