@@ -151,6 +151,7 @@ struct ClsShared {
     uint32_t dfirst[kMaxK];   // first home index that is demoted, per bucket (this round)
     uint64_t dbase[kMaxK];    // pool offset of that demoted block
     uint32_t tbl[kClsTbl];    // (ranking warp, bucket) counts of the round
+    uint32_t mask[kClsTbl];   // (ranking warp, bucket) lanes of the current step, zero between steps
     uint16_t flist[kMaxK];    // buckets whose buffered block completes this round
     uint32_t scan[32];
     uint32_t nflush;
@@ -212,7 +213,10 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
             for (uint64_t g = first + tid; g < last; g += blockDim.x) a.words[ad.slot_base + g] = 0u;
         }
         for (uint32_t b = tid; b < k; b += blockDim.x) sh.run[b] = 0;
-        for (uint32_t j = tid; j < nwr * k; j += blockDim.x) sh.tbl[j] = 0;
+        for (uint32_t j = tid; j < nwr * k; j += blockDim.x) {
+            sh.tbl[j] = 0;
+            sh.mask[j] = 0;
+        }
         if (tid == 0) {
             sh.home_next = 0;
             sh.nflush = 0;
@@ -248,11 +252,18 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                     const uint32_t v = R + (warp * G + e / 4) * 128u + 32u * (e % 4) + lane;
                     const bool valid = v >= delta && v - delta < r;
                     const uint32_t b = bucket_of(group_step_word(words[e / 4], e % 4), k);
-                    const uint32_t peers = warp_peers(b, kbits, valid);
+                    // lanes of this step with the same bucket: OR the lane bits into the warp's row
+                    uint32_t* mrow = sh.mask + warp * k;
+                    if (valid) atomicOr(&mrow[b], 1u << lane);
+                    __syncwarp();
+                    const uint32_t peers = valid ? mrow[b] : 0u;
                     const uint32_t leader = valid ? (uint32_t)(__ffs(peers) - 1) : lane;
                     uint32_t pre = 0;
                     // only this warp touches row `warp`: the returned count is the one before this step
                     if (valid && lane == leader) pre = atomicAdd(&sh.tbl[warp * k + b], (uint32_t)__popc(peers));
+                    __syncwarp();
+                    if (valid && lane == leader) mrow[b] = 0u;
+                    __syncwarp();
                     pre = __shfl_sync(0xffffffffu, pre, (int)leader);
                     bb[e] = valid ? b : 0xffffffffu;
                     rk[e] = pre + __popc(peers & lt_mask);
