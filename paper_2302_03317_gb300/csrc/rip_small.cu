@@ -27,9 +27,10 @@ struct GeneralScratch {         // scatter of a range with several tiles or k > 
     uint32_t run[kMaxK];         // per bucket: elements seen so far in the current tile
     uint32_t tbl[kSmallTbl / 2]; // per (ranking warp, bucket): running count in a round
 };
-struct FastScratch {             // single-tile scatter with k <= 256
-    uint32_t hist[kWarps * 256]; // per (warp, bucket): count, then first output index
-    uint32_t start[256];         // per bucket: total, then first output index of the bucket
+struct FastScratch {               // single-tile scatter with k <= 256
+    uint32_t hist[kWarps * 128];   // per (warp, bucket pair): two 16-bit counts, then first output indices
+    uint32_t start[256];           // per bucket: total, then first output index of the bucket
+    uint32_t mask[kWarps * 64];    // per (warp, low 6 bucket bits): lanes of the current step
 };
 
 constexpr uint32_t kParallelFyMax = (uint32_t)(sizeof(GeneralScratch) / sizeof(uint32_t));
@@ -191,6 +192,7 @@ __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, 
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t k = plan.k[plan.idx(L)];
     const uint32_t kbits = log2_pow2(k);
+    const uint32_t kh = (k + 1u) / 2u;  // packed histogram words per warp
     uint16_t* X = buf ? P1 : P0;
     uint16_t* Y = buf ? P0 : P1;
     const uint64_t o_r = sub_o + a;
@@ -200,7 +202,8 @@ __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, 
     const uint32_t gpw = (ngroups + kWarps - 1) / kWarps;  // groups per warp (<= kFastGroups)
     const uint32_t g0 = warp * gpw;
     uint32_t* hist = sh.f.hist;
-    for (uint32_t j = tid; j < kWarps * k; j += blockDim.x) hist[j] = 0;
+    for (uint32_t j = tid; j < kWarps * kh; j += blockDim.x) hist[j] = 0;
+    for (uint32_t j = tid; j < kWarps * 64u; j += blockDim.x) sh.f.mask[j] = 0;
     __syncthreads();
 
     uint32_t bk[kFastGroups];  // 4 packed 8-bit buckets per group: lane l holds positions 4l .. 4l+3
@@ -217,17 +220,24 @@ __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, 
                 const uint32_t b = bucket_of(w4[j], k);
                 bk[g] |= b << (8 * j);
                 const uint32_t v = v0 + j;
-                if (v >= delta && v - delta < len) atomicAdd(&hist[warp * k + b], 1u);
+                if (v >= delta && v - delta < len) atomicAdd(&hist[warp * kh + (b >> 1)], 1u << (16u * (b & 1u)));
             }
         }
     }
     __syncthreads();
     // rows -> first output index of (warp, bucket)
     for (uint32_t b = tid; b < k; b += blockDim.x) {
+        const uint32_t sh16 = 16u * (b & 1u);
         uint32_t acc = 0;
         for (uint32_t w = 0; w < kWarps; ++w) {
-            const uint32_t c = hist[w * k + b];
-            hist[w * k + b] = acc;
+            uint32_t* cell = &hist[w * kh + (b >> 1)];
+            const uint32_t c = (*cell >> sh16) & 0xFFFFu;
+            // each half-word belongs to one thread: move ours from c to acc without
+            // touching the other half (no borrow or carry crosses the halves)
+            if (acc >= c)
+                atomicAdd(cell, (acc - c) << sh16);
+            else
+                atomicSub(cell, (c - acc) << sh16);
             acc += c;
         }
         sh.f.start[b] = acc;  // bucket total
@@ -241,10 +251,9 @@ __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, 
         if (i1 < k) sh.f.start[i1] = ex + v0;
     }
     __syncthreads();
-    for (uint32_t j = tid; j < kWarps * k; j += blockDim.x) hist[j] += sh.f.start[j & (k - 1u)];  // k is a power of two
-    __syncthreads();
 
     const uint32_t lt_mask = (1u << lane) - 1u;
+    uint32_t* mrow = sh.f.mask + warp * 64u;
 #pragma unroll
     for (uint32_t g = 0; g < kFastGroups; ++g) {
         if (g < gpw && g0 + g < ngroups) {
@@ -255,10 +264,29 @@ __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, 
                 const uint32_t b = (packed >> (8u * (lane & 3u))) & 0xFFu;
                 const uint32_t v = vg + 32u * st + lane;
                 const bool valid = v >= delta && v - delta < len;
-                const uint32_t peers = warp_peers(b, kbits, valid);
+                // lanes with the same bucket: low 6 bits through the warp's mask row, the rest by ballot
+                if (valid) atomicOr(&mrow[b & 63u], 1u << lane);
+                uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+                for (uint32_t i = 6; i < 8; ++i) {
+                    if (i < kbits) {
+                        const uint32_t bit = (b >> i) & 1u;
+                        const uint32_t m = __ballot_sync(0xffffffffu, bit);
+                        peers &= bit ? m : ~m;
+                    }
+                }
+                __syncwarp();
+                peers &= valid ? mrow[b & 63u] : 0u;
                 const uint32_t leader = valid ? (uint32_t)(__ffs(peers) - 1) : lane;
                 uint32_t base = 0;
-                if (valid && lane == leader) base = atomicAdd(&hist[warp * k + b], (uint32_t)__popc(peers));
+                if (valid && lane == leader) {
+                    const uint32_t sh16 = 16u * (b & 1u);
+                    base = ((atomicAdd(&hist[warp * kh + (b >> 1)], (uint32_t)__popc(peers) << sh16) >> sh16) & 0xFFFFu)
+                           + sh.f.start[b];
+                }
+                __syncwarp();
+                if (valid && lane == leader) mrow[b & 63u] = 0u;  // each bucket's leader clears its class
+                __syncwarp();
                 base = __shfl_sync(0xffffffffu, base, (int)leader);
                 if (valid) {
                     const uint32_t d = base + __popc(peers & lt_mask);
@@ -269,7 +297,6 @@ __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, 
         }
     }
     __syncthreads();
-    // bucket starts survive in sh.f.start[0..k)
     finish_children(sh, P0, Y, a, len, k, L, buf, plan, key, o_r, status,
                     [&](uint32_t b) { return sh.f.start[b]; });
     return true;
