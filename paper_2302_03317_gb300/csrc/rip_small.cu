@@ -51,12 +51,35 @@ __device__ __forceinline__ uint64_t pack_range(uint32_t a, uint32_t len, uint32_
     return (uint64_t)a | ((uint64_t)len << 20) | ((uint64_t)L << 40) | ((uint64_t)buf << 48);
 }
 
-// One Fisher-Yates pass over Z[0..len) by the calling thread (Sec. 2.2).
-__device__ void fy_serial(uint16_t* Z, uint32_t len, PhiloxKey key, uint32_t L, uint64_t leaf_o) {
-    FyStream fs;
-    fs.init(key, L, leaf_o);
+// Lemire acceptance for s < 2^32 in 32-bit arithmetic (same decisions as lemire_accept).
+__device__ __forceinline__ bool lemire32(uint32_t x, uint32_t s, uint32_t& v) {
+    const uint64_t m = (uint64_t)x * s;
+    const uint32_t lo = (uint32_t)m;
+    if (lo < s && lo < (0u - s) % s) return false;
+    v = (uint32_t)(m >> 32);
+    return true;
+}
+
+// Fisher-Yates over Z[0..len) by the calling thread (Sec. 2.2): all partner
+// draws first (one Philox call per four positions, independent iterations),
+// stored in H[1..len), then the dependent swap chain.  len < 2^16.
+__device__ void fy_thread(uint16_t* Z, uint16_t* H, uint32_t len, PhiloxKey key, uint32_t L, uint64_t leaf_o) {
+    const uint64_t q_first = (leaf_o + 1) >> 2, q_last = (leaf_o + len - 1) >> 2;
+    for (uint64_t q = q_first; q <= q_last; ++q) {
+        const uint4 r = philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), L | (kTagFy << 8), (uint32_t)leaf_o, key);
+        const uint32_t w4[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (uint32_t wd = 0; wd < 4; ++wd) {
+            const uint64_t i64 = 4 * q + wd - leaf_o;  // step index of this word
+            if (4 * q + wd < leaf_o + 1 || i64 >= len) continue;
+            const uint32_t i = (uint32_t)i64;
+            uint32_t v;
+            if (!lemire32(w4[wd], i + 1, v)) v = (uint32_t)fy_draw_retry(key, L, leaf_o, leaf_o + i, i + 1);
+            H[i] = (uint16_t)v;
+        }
+    }
     for (uint32_t i = len - 1; i >= 1; --i) {
-        const uint32_t j = (uint32_t)fs.draw(i);
+        const uint32_t j = H[i];
         const uint16_t zi = Z[i];
         Z[i] = Z[j];
         Z[j] = zi;
@@ -149,9 +172,9 @@ __device__ void fy_block(uint16_t* Z, uint16_t* draws, uint32_t len, PhiloxKey k
 // Children of a scattered range: leaves are finished right away, larger ones
 // are pushed for another scatter.  start(b) = first output index of bucket b.
 template <typename StartFn>
-__device__ void finish_children(SmallShared& sh, uint16_t* P0, uint16_t* Y, uint32_t a, uint32_t len, uint32_t k,
-                                uint32_t L, uint32_t buf, const DevPlan& plan, PhiloxKey key, uint64_t o_r,
-                                Status* status, StartFn start) {
+__device__ void finish_children(SmallShared& sh, uint16_t* P0, uint16_t* X, uint16_t* Y, uint32_t a, uint32_t len,
+                                uint32_t k, uint32_t L, uint32_t buf, const DevPlan& plan, PhiloxKey key,
+                                uint64_t o_r, Status* status, StartFn start) {
     for (uint32_t b = threadIdx.x; b < k; b += blockDim.x) {
         const uint32_t sb = start(b);
         const uint32_t se = b + 1 < k ? start(b + 1) : len;
@@ -163,7 +186,8 @@ __device__ void finish_children(SmallShared& sh, uint16_t* P0, uint16_t* Y, uint
         }
         if (size == 1 || plan.is_leaf(size, L + 1)) {
             uint16_t* Z = Y + a + sb;
-            if (size > 1) fy_serial(Z, size, key, L + 1, o_r + sb);
+            // the scatter's source range is free now: it holds the child's draws
+            if (size > 1) fy_thread(Z, X + a + sb, size, key, L + 1, o_r + sb);
             if (Y != P0)
                 for (uint32_t j = 0; j < size; ++j) P0[a + sb + j] = Z[j];
         } else {
@@ -297,7 +321,7 @@ __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, 
         }
     }
     __syncthreads();
-    finish_children(sh, P0, Y, a, len, k, L, buf, plan, key, o_r, status,
+    finish_children(sh, P0, X, Y, a, len, k, L, buf, plan, key, o_r, status,
                     [&](uint32_t b) { return sh.f.start[b]; });
     return true;
 }
@@ -455,7 +479,7 @@ __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint3
     }
 
     // children: leaves now, larger ones onto the stack (tile 0 entry of fb = s_b)
-    finish_children(sh, P0, Y, a, len, k, L, buf, plan, key, o_r, status, [&](uint32_t b) { return sh.g.fb[b]; });
+    finish_children(sh, P0, X, Y, a, len, k, L, buf, plan, key, o_r, status, [&](uint32_t b) { return sh.g.fb[b]; });
 }
 
 template <int W>
@@ -537,7 +561,11 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(SmallArgs args) {
             }
         }
         __syncthreads();
-        for (uint32_t i = tid; i < m; i += blockDim.x) base[s.o + i] = D[P0[i]];
+        for (uint32_t i = tid; i < m; i += blockDim.x) {
+            const uint32_t j = P0[i];
+            if (j < m) base[s.o + i] = D[j];
+            else report(args.status, RIP_EINTERNAL, 0x5107, j);  // never read outside the subproblem
+        }
         __syncthreads();
     }
 }
