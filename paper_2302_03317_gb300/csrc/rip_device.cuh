@@ -65,6 +65,32 @@ __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_
     return make_uint4(c0, c1, c2, c3);
 }
 
+// Philox with the ten round keys computed once (they depend on the seed only).
+struct PhiloxKeys {
+    uint32_t k0[10], k1[10];
+    __device__ __forceinline__ void init(PhiloxKey key) {
+#pragma unroll
+        for (int r = 0; r < 10; ++r) {
+            k0[r] = key.k0 + (uint32_t)r * 0x9E3779B9u;
+            k1[r] = key.k1 + (uint32_t)r * 0xBB67AE85u;
+        }
+    }
+};
+
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                               const PhiloxKeys& ks) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        c0 = (uint32_t)(p1 >> 32) ^ c1 ^ ks.k0[r];
+        c2 = (uint32_t)(p0 >> 32) ^ c3 ^ ks.k1[r];
+        c1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
 __device__ __forceinline__ PhiloxKey make_key(uint64_t seed) {
     return PhiloxKey{(uint32_t)seed, (uint32_t)(seed >> 32)};
 }
@@ -102,6 +128,11 @@ __device__ __forceinline__ uint32_t warp_scatter_word(PhiloxKey key, uint32_t le
 __device__ __forceinline__ uint4 group_philox(PhiloxKey key, uint32_t level, uint64_t o, uint64_t Qg) {
     const uint64_t q = Qg + (threadIdx.x & 31u);
     return philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), level | (kTagScatter << 8), (uint32_t)o, key);
+}
+
+__device__ __forceinline__ uint4 group_philox(const PhiloxKeys& ks, uint32_t level, uint64_t o, uint64_t Qg) {
+    const uint64_t q = Qg + (threadIdx.x & 31u);
+    return philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), level | (kTagScatter << 8), (uint32_t)o, ks);
 }
 
 __device__ __forceinline__ uint32_t group_step_word(const uint4& r, uint32_t s) {

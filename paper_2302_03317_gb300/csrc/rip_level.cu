@@ -176,6 +176,8 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
     T* buf = reinterpret_cast<T*>(smem_raw + ((sizeof(ClsShared) + 15) & ~size_t(15)));
     const uint32_t k = a.k, B = a.B, L = a.level;
     const uint32_t kbits = log2_pow2(k);
+    const bool bpow2 = (B & (B - 1u)) == 0;
+    const uint32_t bshift = log2_pow2(B);
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t nwarps = blockDim.x >> 5;
     const uint32_t nwr = min(nwarps, kClsTbl / k);
@@ -192,7 +194,8 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
         const Sub S = a.big[tr.sp];
         const ArrayDesc ad = a.arrays[S.arr];
         T* base = reinterpret_cast<T*>(ad.data);
-        const PhiloxKey key = make_key(ad.seed);
+        PhiloxKeys pk;
+        pk.init(make_key(ad.seed));
         const uint64_t lo = (uint64_t)tr.t * a.T;
         const uint32_t r = (uint32_t)(min(lo + a.T, S.m) - lo);
         const uint64_t alo = S.o + S.eps + lo;  // physical start of the tile's aligned piece
@@ -221,14 +224,25 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
             sh.home_next = 0;
             sh.nflush = 0;
         }
-        T val[E], nxt[E];
-        if (warp < nwr) {
+        // elements [0, avail) of the tile are contiguous at base + alo; the rest (the
+        // rotation's wrap piece) goes through phys_index
+        const T* tile_ptr = base + alo;
+        auto load_round = [&](T (&dst)[E], uint32_t Rv) {
+            const uint32_t v0 = Rv + warp * G * 128u + lane;  // position of element e = 0
+            if (v0 >= delta && Rv + (warp * G + G) * 128u <= avail + delta) {
+                const T* p = tile_ptr + (v0 - delta);
 #pragma unroll
-            for (uint32_t e = 0; e < E; ++e) {
-                const uint32_t v = (warp * G + e / 4) * 128u + 32u * (e % 4) + lane;
-                if (v >= delta && v - delta < r) nxt[e] = base[phys_index(S, lo + (v - delta))];
+                for (uint32_t e = 0; e < E; ++e) dst[e] = p[(e / 4) * 128u + 32u * (e % 4)];
+            } else {
+#pragma unroll
+                for (uint32_t e = 0; e < E; ++e) {
+                    const uint32_t v = v0 + (e / 4) * 128u + 32u * (e % 4);
+                    if (v >= delta && v - delta < r) dst[e] = base[phys_index(S, lo + (v - delta))];
+                }
             }
-        }
+        };
+        T val[E], nxt[E];
+        if (warp < nwr) load_round(nxt, 0);
         __syncthreads();
 
         for (uint32_t R = 0; R < rv; R += round) {
@@ -236,17 +250,11 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
             if (warp < nwr) {
 #pragma unroll
                 for (uint32_t e = 0; e < E; ++e) val[e] = nxt[e];
-                if (R + round < rv) {
-#pragma unroll
-                    for (uint32_t e = 0; e < E; ++e) {
-                        const uint32_t v = R + round + (warp * G + e / 4) * 128u + 32u * (e % 4) + lane;
-                        if (v - delta < r) nxt[e] = base[phys_index(S, lo + (v - delta))];
-                    }
-                }
+                if (R + round < rv) load_round(nxt, R + round);
                 uint4 words[G];
 #pragma unroll
                 for (uint32_t g = 0; g < G; ++g)
-                    words[g] = group_philox(key, L, S.o, Q0 + (R >> 2) + (warp * G + g) * 32u);
+                    words[g] = group_philox(pk, L, S.o, Q0 + (R >> 2) + (warp * G + g) * 32u);
 #pragma unroll
                 for (uint32_t e = 0; e < E; ++e) {
                     const uint32_t v = R + (warp * G + e / 4) * 128u + 32u * (e % 4) + lane;
@@ -275,16 +283,20 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
             // blocks, home slots, demotion
             for (uint32_t b = tid; b < k; b += blockDim.x) {
                 uint32_t tot = 0;
-                for (uint32_t w = 0; w < nwr; ++w) {
-                    const uint32_t c = sh.tbl[w * k + b];
-                    sh.tbl[w * k + b] = tot;
-                    tot += c;
-                }
+                for (uint32_t w = 0; w < nwr; ++w) tot += sh.tbl[w * k + b];
                 const uint32_t rb = sh.run[b], nr = rb + tot;
                 sh.newrun[b] = nr;
                 const uint32_t cb = a.fdB.div(rb), eb = a.fdB.div(nr);
                 const uint32_t rem = rb - cb * B;
                 sh.binfo[b] = rem | ((eb - cb) << 16);
+                // per (warp, bucket): offset of the warp's first element in the bucket's
+                // current partial block (< 2^16), and the number of completing blocks
+                uint32_t acc = rem;
+                for (uint32_t w = 0; w < nwr; ++w) {
+                    const uint32_t c = sh.tbl[w * k + b];
+                    sh.tbl[w * k + b] = acc | ((eb - cb) << 16);
+                    acc += c;
+                }
                 if (eb > cb) {
                     const uint32_t nb = eb - cb;
                     const uint32_t hs = atomicAdd(&sh.home_next, nb);
@@ -325,13 +337,13 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                     const uint32_t b = bb[e];
                     if (b == 0xffffffffu) continue;
                     // offset inside the bucket's current partial block, counted from its start
-                    const uint32_t bi = sh.binfo[b];
-                    const uint32_t rem = bi & 0xFFFFu;
-                    const uint32_t local = rem + sh.tbl[warp * k + b] + rk[e];
-                    const uint32_t q = a.fdB.div(local), pos = local - q * B;
+                    const uint32_t we = sh.tbl[warp * k + b];
+                    const uint32_t local = (we & 0xFFFFu) + rk[e];
+                    const uint32_t q = bpow2 ? local >> bshift : a.fdB.div(local);
+                    const uint32_t pos = local - q * B;
                     rk[e] = pos;
-                    if (q < (bi >> 16)) {
-                        if (q == 0 && rem != 0) {
+                    if (q < (we >> 16)) {
+                        if (q == 0 && (sh.binfo[b] & 0xFFFFu) != 0) {
                             buf[b * B + pos] = val[e];
                         } else {
                             const uint32_t h = sh.hsb[b] + q;
