@@ -108,6 +108,22 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(ms: float, dist=None, device=None) -> float:
+    """The slowest rank's time (replicas: the job ends when the last one does)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world_size: int, n_per_rank: int, ms_per_step: float) -> float:
+    """Whole-job throughput of independent replicas (weak scaling): every rank
+    shuffles its own n_per_rank elements per step."""
+    return world_size * n_per_rank / (ms_per_step / 1e3)
+
+
 def cpu_oracle_sample(plan, log2n: int):
     """Times the CPU oracle (single thread, as it stands) on 2^log2n u64 iota."""
     import numpy as np
@@ -230,13 +246,9 @@ def main():
     if rc != 0:
         raise SystemExit(f"device status after timed steps: {rip.rip_strerror(rc)}")
     prof = rip.rip_profile_get()
-    t_max = ms_total
-    if dist is not None:
-        tt = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(ms_total, dist, "cuda")
     ms_per_step = t_max / args.steps
-    value = ws * n / (ms_per_step / 1e3)
+    value = job_rate(ws, n, ms_per_step)
 
     # roofline of the dominant kernel: algorithmic bytes = one read + one write of
     # every element the launch processes (each of these kernels touches the whole
@@ -278,12 +290,8 @@ def main():
         h1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        e_ms = h0.elapsed_time(h1) / args.steps
-        if dist is not None:
-            tt = torch.tensor([e_ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e_ms = float(tt.item())
-        e2e = {"value": ws * n / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": n * w,
+        e_ms = max_over_ranks(h0.elapsed_time(h1) / args.steps, dist, "cuda")
+        e2e = {"value": job_rate(ws, n, e_ms), "unit": UNIT, "h2d_bytes_per_step": n * w,
                "d2h_bytes_per_step": n * w, "ms_per_step": e_ms}
         del host
 

@@ -88,7 +88,7 @@ namespace {
 
 constexpr uint32_t kMediumGrid = 16;
 constexpr uint32_t kParkAfter = 256;  // chain steps before the permutation parks a block
-constexpr size_t kClassifySmemBudget = 200 * 1024;
+constexpr size_t kClassifySmemBudget = 224 * 1024;
 
 struct LevelCaps {
     uint32_t big = 0;       // subproblems that may run in place

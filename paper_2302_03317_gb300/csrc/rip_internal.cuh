@@ -11,8 +11,8 @@ constexpr uint32_t kSmallCntCap = 512;    // (tile, bucket) counters of one in-S
 constexpr uint32_t kSmallTbl = 4096;      // (ranking warp, bucket) entries
 constexpr uint32_t kSmallStack = 256;     // pending scatter ranges inside one subproblem
 constexpr uint32_t kMediumMaxM = 49152;   // largest subproblem finished on one SM
-constexpr uint32_t kClassifyThreads = 512;
-constexpr uint32_t kClsTbl = 4096;
+constexpr uint32_t kClassifyThreads = 1024;
+constexpr uint32_t kClsTbl = 8192;   // (ranking warp, bucket) entries: 32 warps x 256
 constexpr uint32_t kPermuteThreads = 256;
 constexpr uint32_t kGroup = 8;            // lanes moving one block in the permutation
 constexpr size_t kSmemOptin = 232448;     // dynamic shared memory per block on sm_100/103

@@ -194,8 +194,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
         const Sub S = a.big[tr.sp];
         const ArrayDesc ad = a.arrays[S.arr];
         T* base = reinterpret_cast<T*>(ad.data);
-        PhiloxKeys pk;
-        pk.init(make_key(ad.seed));
+        const PhiloxKey pk = make_key(ad.seed);
         const uint64_t lo = (uint64_t)tr.t * a.T;
         const uint32_t r = (uint32_t)(min(lo + a.T, S.m) - lo);
         const uint64_t alo = S.o + S.eps + lo;  // physical start of the tile's aligned piece
@@ -402,6 +401,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
 
         // tails of every bucket -> pool; counts and tile info
         {
+            // k <= kMaxK <= 2 * blockDim.x: two buckets per thread
             const uint32_t i0 = 2 * tid, i1 = 2 * tid + 1;
             const uint32_t r0 = i0 < k ? a.fdB.mod(sh.run[i0]) : 0, r1 = i1 < k ? a.fdB.mod(sh.run[i1]) : 0;
             uint32_t total;
@@ -876,7 +876,7 @@ cudaError_t launch_init(const InitArgs& a, cudaStream_t s) {
 
 template <int W>
 static cudaError_t launch_level_w(const LevelArgs& a, uint32_t num_sms, cudaStream_t s, uint32_t* launches) {
-    constexpr int E = W == 16 ? 1 : 2;  // groups of 128 positions per ranking warp per round
+    constexpr int E = 1;  // groups of 128 positions per ranking warp per round
     cudaError_t err;
     {
         ProfScope p("tiles", s);
