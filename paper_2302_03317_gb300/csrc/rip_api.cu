@@ -140,7 +140,8 @@ int validate_plan(const rip_plan& p, uint32_t w) {
         const rip_level_params& q = p.level[l];
         if (!pow2(q.k) || q.k < 2 || q.k > kMaxK) return RIP_EINVAL;
         if (q.block < 1 || q.tile < q.block || q.tile % q.block) return RIP_EINVAL;
-        if (classify_smem_bytes(q.k, q.block, w) > kClassifySmemBudget) return RIP_EINVAL;
+        ClsCfg cc;
+        if (!classify_config(q.k, q.block, w, &cc)) return RIP_EINVAL;
         if (l > 0 && p.level[l - 1].block % q.block) return RIP_EINVAL;  // slot grids must nest
     }
     return RIP_OK;
@@ -237,6 +238,13 @@ Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& 
                                       : dem_worst;
         c.dem = (uint64_t)dem_worst + 16;
         c.pool = (uint64_t)(tails + dem_blocks * B) + 64;
+        // chunked staging: a block's location is taken at its first chunk, from the pool while
+        // no read home slot is free -- at most k such blocks per tile
+        ClsCfg cc{};
+        if (classify_config(k, B, w, &cc) && cc.cpb > 1) {
+            c.pool += c.tiles * k * B;
+            c.dem += c.tiles * k;
+        }
         max_children = std::max<uint64_t>(max_children, (uint64_t)c.big * k);
         caps.push_back(c);
         small_children += (uint64_t)c.big * k;
@@ -487,6 +495,7 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
         a.fdB = FastDiv::make(a.B);
         if (!fastdiv_ok(a.fdB)) return RIP_EINTERNAL;
         a.vec16 = aligned16 && ((a.B * w) % 16 == 0) ? 1u : 0u;
+        if (!classify_config(a.k, a.B, w, &a.cls)) return RIP_EINVAL;
         a.big = lists.big[lev & 1];
         a.big_count = lists.big_count[lev & 1];
         a.next_big = lists.big[(lev + 1) & 1];

@@ -1,0 +1,729 @@
+// rip_classify.cu -- the classify step of one in-place scatter level.
+//
+// One CTA streams one tile of T elements (Sec. 3.1: every element draws its
+// bucket, Sec. 2.2; elements of one bucket keep their input order inside the
+// tile).  Bucket b's elements form a stream; its j-th B-element block is the
+// stream's elements [jB, (j+1)B).  Every completed block is written back into
+// the tile's own front, which has already been read ("home slots", the
+// in-place block buffers of Sec. 3.5), or, while no read home slot is free,
+// into a small pool; the remainder of every stream (fewer than B elements) is
+// the tile's tail for that bucket and goes to the pool at the end of the tile.
+//
+// Per round of nwr*128 consecutive positions:
+//   load     the round's elements arrive in a shared-memory buffer by a bulk
+//            (TMA) copy one or two rounds ahead, completing on an mbarrier;
+//            ragged edges (unaligned ends, the rotation's wrap piece) are
+//            copied by the threads
+//   rank     Philox bucket draws (a1), stable ranks per bucket: the lanes of a
+//            step with the same bucket come from one ballot per bucket bit,
+//            the warp's running count per bucket lives in a (bucket, warp)
+//            table of 16-bit counters (a2)
+//            -- meanwhile the chunks completed by the previous round are
+//               written out, so stores overlap the arithmetic
+//   book     per bucket: exclusive prefix over the ranking warps (one warp
+//            scans 32/nwr buckets at once), blocks completed, home slots or
+//            pool blocks for blocks that receive data, slot words
+//   place    every element goes to its bucket's shared-memory chunk (Bs
+//            elements, Bs divides B), straight to its block in global memory
+//            when its whole chunk lies inside this round, or is carried into
+//            the next round when it starts a chunk that completes later
+//
+// A block gets its location when its first chunk is written.  A home slot h
+// may be used once the tile's elements [0, (h+1)B) have been read; otherwise
+// (at the start of a tile, when chunks are smaller than blocks) the block goes
+// to the pool.  At most k blocks per tile take the pool that way: every
+// allocated block except the <= k open ones is complete, and the home slots
+// only lag the consumed elements by less than one block.
+#include "rip_internal.cuh"
+
+namespace rip {
+
+namespace {
+
+constexpr uint64_t kLocPool = 1ull << 63;  // location in the pool (else: element index in the array)
+constexpr uint32_t kNone = 0xffffffffu;
+constexpr uint32_t kWaitLimit = 1u << 26;  // mbarrier polls before giving up
+
+struct ClsMisc {
+    uint64_t full[3];      // input buffer loaded (transaction count of the bulk copy)
+    uint64_t stage_free;   // the I/O warp has read out the chunks completed by the previous round
+    uint64_t flush_ready;  // the compute warps have placed a round
+    uint64_t pool_base;
+    uint32_t tile;
+    uint32_t home_next;
+    uint32_t nflush[2];
+    uint32_t fail;
+    uint32_t scan[32];
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false after kWaitLimit polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_addr(bar);
+    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// One bulk copy global -> shared, completing `bytes` transactions on `bar`.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// One bulk copy shared -> global (the TMA engine reads the chunk; no per-lane stores).
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the sources of this thread's bulk stores have been read (shared memory may be rewritten)
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// this thread's bulk stores are complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// order this thread's generic shared-memory writes before later async-proxy reads of them
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+// Lanes of the warp with the same bucket as the calling lane (among valid lanes): one
+// ballot per bucket bit; KB > 0 fixes the bit count at compile time.
+template <int KB>
+__device__ __forceinline__ uint32_t bucket_peers(uint32_t b, bool valid, uint32_t kbits) {
+    uint32_t peers = __ballot_sync(0xffffffffu, valid);
+    if constexpr (KB > 0) {
+#pragma unroll
+        for (int i = 0; i < KB; ++i) {
+            const bool bit = (b >> i) & 1u;
+            const uint32_t m = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? m : ~m;
+        }
+    } else {
+        for (uint32_t i = 0; i < kbits; ++i) {
+            const bool bit = (b >> i) & 1u;
+            const uint32_t m = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? m : ~m;
+        }
+    }
+    return peers;
+}
+
+// Geometry that depends on k only (the same formulas as classify_config): warp 31 does the
+// bulk copies, warps 0..30 compute; nwr of them rank (the table holds k * nwr counters).
+constexpr uint32_t kIoWarp = kClassifyThreads / 32u - 1u;
+constexpr uint32_t kComputeThreads = kIoWarp * 32u;
+// 16-byte records rank with 16 warps: rounds half as long keep whole blocks staged
+__host__ __device__ constexpr uint32_t cls_nwr(uint32_t k, uint32_t w) {
+    return 8192u / k < (w >= 16 ? 16u : kIoWarp) ? 8192u / k : (w >= 16 ? 16u : kIoWarp);
+}
+__host__ __device__ constexpr uint32_t cls_stride(uint32_t k, uint32_t w) { return (cls_nwr(k, w) + 1u) | 1u; }  // odd
+
+__device__ __forceinline__ void compute_sync() {
+    asm volatile("bar.sync 1, %0;" ::"r"(kComputeThreads) : "memory");
+}
+
+// A flush entry: bucket in bits 48..57, the chunk's destination location in the rest.
+constexpr uint64_t kEntLoc = ~(0x3FFull << 48);
+
+// KB = log2 k for the specialised kernels, 0: k from the arguments.
+template <int W, int KB>
+__global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs a) {
+    using T = typename Elem<W>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const ClsCfg g = a.cls;
+    constexpr uint32_t KC = KB > 0 ? (1u << KB) : 0u;
+    ClsMisc& ms = *reinterpret_cast<ClsMisc*>(smem_raw);
+    uint16_t* tbl = reinterpret_cast<uint16_t*>(smem_raw + g.off_tbl);
+    uint32_t* run = reinterpret_cast<uint32_t*>(smem_raw + g.off_u32);
+    const uint32_t k = KB > 0 ? KC : a.k;
+    const uint32_t nwr = KB > 0 ? cls_nwr(KC, W) : g.nwr;
+    const uint32_t S = KB > 0 ? cls_stride(KC, W) : g.S;
+    const uint32_t B = a.B, L = a.level, Bs = g.Bs, cpb = g.cpb;
+    uint32_t* rb = run + k;      // stream length before the current round
+    uint32_t* oblk = rb + k;     // block index of the open block (kNone: none)
+    uint32_t* jnew = oblk + k;   // first block allocated this round
+    uint32_t* take = jnew + k;   // of which this many got home slots
+    uint32_t* hbase = take + k;  // first of those home slots
+    uint64_t* optr = reinterpret_cast<uint64_t*>(smem_raw + g.off_u64);  // location of the open block
+    uint64_t* jloc = optr + k;   // location of the block holding the round's first chunk
+    uint64_t* pbase = jloc + k;  // pool location of the round's first pool block
+    uint64_t* flist = reinterpret_cast<uint64_t*>(smem_raw + g.off_flist);  // 2 x k flush entries
+    T* stage = reinterpret_cast<T*>(smem_raw + g.off_stage);
+    T* bufs = reinterpret_cast<T*>(smem_raw + g.off_buf);
+
+    const uint32_t kbits = KB > 0 ? (uint32_t)KB : log2_pow2(k);
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const bool io = warp == kIoWarp;
+    const uint32_t round = nwr * 128u, q = g.q, nbuf = g.nbuf;
+    const uint32_t ntiles = a.counters[0];
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const bool bs_pow2 = (Bs & (Bs - 1u)) == 0;
+    const uint32_t bs_shift = log2_pow2(Bs);
+    const bool b_pow2 = (B & (B - 1u)) == 0;
+    const uint32_t b_shift = log2_pow2(B);
+    const bool flush_vec = a.vec16 && (Bs * W) % 16u == 0;
+    T* pool = reinterpret_cast<T*>(a.pool);
+
+    if (tid == 0) {
+        for (uint32_t i = 0; i < nbuf; ++i) mbar_init(&ms.full[i], 1);
+        mbar_init(&ms.stage_free, 1);
+        mbar_init(&ms.flush_ready, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        ms.fail = 0;
+    }
+    __syncthreads();
+
+    // completions so far of: the input buffers (one per round), stage_free (one per round and
+    // one per tile), flush_ready (one per round); every thread counts the same way
+    uint32_t grc = 0, sfc = 0, frc = 0;
+    for (;;) {
+        if (tid == 0) ms.tile = atomicAdd(&a.counters[1], 1u);
+        __syncthreads();
+        const uint32_t tile = ms.tile;
+        if (tile >= ntiles || ms.fail) break;
+        const TileRef tr = a.tiles[tile];
+        const Sub Sp = a.big[tr.sp];
+        const ArrayDesc ad = a.arrays[Sp.arr];
+        T* base = reinterpret_cast<T*>(ad.data);
+        const PhiloxKey pk = make_key(ad.seed);
+        const uint64_t lo = (uint64_t)tr.t * a.T;
+        const uint32_t r = (uint32_t)(min(lo + a.T, Sp.m) - lo);
+        const uint64_t alo = Sp.o + Sp.eps + lo;  // physical start of the tile's aligned piece
+        const uint32_t avail = Sp.m > Sp.eps + lo ? (uint32_t)min((uint64_t)r, Sp.m - Sp.eps - lo) : 0u;
+        const uint32_t H = avail / B;
+        const uint64_t hs0 = ad.slot_base + alo / B;
+        const uint64_t P0 = Sp.o + lo;  // logical global position of the tile's first element
+        const uint32_t delta = (uint32_t)(P0 & 3u);
+        const uint64_t Q0 = P0 >> 2;
+        const uint32_t rv = r + delta;  // positions covered, counted from 4*Q0
+        const uint32_t nrounds = (rv + round - 1) / round;
+        if (alo % B != 0 && tid == 0) report(a.status, RIP_EINTERNAL, 0x6201, alo);
+
+        // Slots of this level's grid inside the leading wrap piece [o, o+eps) lie in the
+        // region but in no tile's home range (only when B is smaller than the parent's):
+        // mark them empty so the permutation may fill them.
+        if (tr.t == 0 && Sp.eps >= B) {
+            const uint64_t first = (Sp.o + B - 1) / B, last = (Sp.o + Sp.eps) / B;
+            for (uint64_t x = first + tid; x < last; x += blockDim.x) a.words[ad.slot_base + x] = 0u;
+        }
+        for (uint32_t b = tid; b < k; b += blockDim.x) {
+            run[b] = 0;
+            oblk[b] = kNone;
+        }
+        // every home slot starts empty; completed blocks fill in their words
+        for (uint32_t h = tid; h < H; h += blockDim.x) a.words[hs0 + h] = 0u;
+        for (uint32_t j = tid; j < k * S; j += blockDim.x) tbl[j] = 0;
+        if (tid == 0) {
+            ms.home_next = 0;
+            ms.nflush[0] = ms.nflush[1] = 0;
+        }
+        __syncthreads();
+
+        // round rr holds tile elements [R - delta, R - delta + round) at buffer index
+        // (element - (R - delta) + shift), shift chosen so bulk copies start 16-byte aligned
+        auto shift_of = [&](uint32_t rr) -> uint32_t {
+            return (uint32_t)((alo + (uint64_t)rr * round - delta) & (uint64_t)(q - 1u));
+        };
+        auto loc_ptr = [&](uint64_t loc) -> T* {
+            return (loc & kLocPool) ? pool + (loc & ~kLocPool) : base + loc;
+        };
+        uint32_t carried[4] = {kNone, kNone, kNone, kNone};
+        uint32_t carried_buf = 0;  // buffer of the carried elements
+
+        if (io) {
+            // ---------------------------------------------------------------- I/O warp
+            // load of round rr into buffer (grc + rr) % nbuf: bulk copy for the aligned inside,
+            // the lanes copy ragged ends and the rotation's wrap piece
+            auto load = [&](uint32_t rr) {
+                const uint32_t gr = grc + rr;
+                T* buf = bufs + (size_t)(gr % nbuf) * g.bufstride;
+                const uint32_t R = rr * round;
+                const uint32_t sh = shift_of(rr);
+                const int64_t e0 = (int64_t)R - (int64_t)delta;  // element of buffer index `sh`
+                const uint32_t e_lo = e0 > 0 ? (uint32_t)e0 : 0u;
+                const int64_t e_end = e0 + (int64_t)round;
+                const uint32_t e_hi = e_end < (int64_t)r ? (uint32_t)e_end : r;
+                const uint32_t a_hi = min(e_hi, avail);
+                uint32_t b_lo = e_lo, b_hi = e_lo;  // bulk part [b_lo, b_hi), inside the aligned piece
+                if (a_hi > e_lo) {
+                    const uint32_t mis = (uint32_t)((alo + e_lo) & (uint64_t)(q - 1u));
+                    b_lo = e_lo + (mis ? q - mis : 0u);
+                    b_hi = a_hi - (uint32_t)((alo + a_hi) & (uint64_t)(q - 1u));
+                    if (b_hi <= b_lo || !a.vec16) b_lo = b_hi = e_lo;
+                }
+                for (uint32_t e = e_lo + lane; e < b_lo; e += 32u)
+                    buf[(uint32_t)((int64_t)e - e0) + sh] = base[alo + e];
+                for (uint32_t e = b_hi + lane; e < e_hi; e += 32u)
+                    buf[(uint32_t)((int64_t)e - e0) + sh] = e < avail ? base[alo + e] : base[phys_index(Sp, lo + e)];
+                __syncwarp();
+                if (lane == 0) {
+                    if (b_hi > b_lo) {
+                        const uint32_t bytes = (b_hi - b_lo) * (uint32_t)W;
+                        mbar_arrive_expect_tx(&ms.full[gr % nbuf], bytes);
+                        bulk_g2s(buf + ((uint32_t)((int64_t)b_lo - e0) + sh), base + alo + b_lo, bytes,
+                                 &ms.full[gr % nbuf]);
+                    } else {
+                        mbar_arrive(&ms.full[gr % nbuf]);
+                    }
+                }
+            };
+            for (uint32_t rr = 0; rr + 1 < nbuf && rr < nrounds; ++rr) load(rr);
+            if (lane == 0) mbar_arrive(&ms.stage_free);  // round 0 may place: nothing to flush yet
+            for (uint32_t rr = 0; rr < nrounds; ++rr) {
+                // round rr is placed: its chunks and flush list are ready, the buffer of rr-1 is free
+                uint32_t ok = 1;
+                if (lane == 0) ok = mbar_wait(&ms.flush_ready, (frc + rr) & 1u);
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                __syncwarp();  // lane 0's acquire covers the whole warp
+                if (!ok) {
+                    if (lane == 0) report(a.status, RIP_ETIMEOUT, 0x6208, rr);
+                    ms.fail = 1;
+                }
+                if (!ok || ms.fail) break;
+                if (rr + nbuf - 1 < nrounds) load(rr + nbuf - 1);
+                const uint32_t par = rr & 1u;
+                const uint32_t nf = ms.nflush[par];
+                const uint64_t* fl = flist + par * k;
+                bool issued = false;
+                if (flush_vec) {
+                    for (uint32_t f = lane; f < nf; f += 32u) {
+                        const uint64_t e = fl[f];
+                        const uint32_t b = (uint32_t)(e >> 48) & 0x3FFu;
+                        const uint64_t loc = e & kEntLoc;
+                        if ((loc & kLocPool) && (loc & ~kLocPool) + Bs > a.pool_cap) continue;  // reported
+                        bulk_s2g(loc_ptr(loc), stage + (size_t)b * Bs, Bs * (uint32_t)W);
+                        issued = true;
+                    }
+                    if (issued) {
+                        bulk_commit();
+                        if (rr + 1 == nrounds) {
+                            bulk_wait_all();  // the tails read open blocks back
+                            fence_proxy_async_global();
+                        } else {
+                            bulk_wait_read();
+                        }
+                    }
+                } else {
+                    for (uint32_t f = 0; f < nf; ++f) {
+                        const uint64_t e = fl[f];
+                        const uint32_t b = (uint32_t)(e >> 48) & 0x3FFu;
+                        const uint64_t loc = e & kEntLoc;
+                        if ((loc & kLocPool) && (loc & ~kLocPool) + Bs > a.pool_cap) continue;  // reported
+                        T* dst = loc_ptr(loc);
+                        const T* src = stage + (size_t)b * Bs;
+                        for (uint32_t u = lane; u < Bs; u += 32u) dst[u] = src[u];
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&ms.stage_free);  // the chunks are read out: round rr+1 may place
+            }
+        } else {
+            // ---------------------------------------------------------------- compute warps
+            for (uint32_t rr = 0; rr < nrounds; ++rr) {
+                const uint32_t R = rr * round;
+                const uint32_t gr = grc + rr;
+                const uint32_t par = rr & 1u;
+                if (tid == 0) ms.nflush[par] = 0;
+
+                // rank: lanes of a step with the same bucket read the warp's running count
+                // together, the lowest of them writes it back advanced by their number
+                uint32_t packed[4] = {kNone, kNone, kNone, kNone};
+                if (warp < nwr) {
+                    const uint4 words = group_philox(pk, L, Sp.o, Q0 + (R >> 2) + warp * 32u);
+                    const uint32_t v0 = R + warp * 128u + lane;
+                    const bool interior = R >= delta && R + round <= rv;  // every position is valid
+#pragma unroll
+                    for (uint32_t s = 0; s < 4; ++s) {
+                        const uint32_t v = v0 + 32u * s;
+                        const bool valid = interior || (v >= delta && v - delta < r);
+                        const uint32_t b = bucket_of(group_step_word(words, s), k);
+                        const uint32_t peers = bucket_peers<KB>(b, valid, kbits);
+                        uint16_t* c = tbl + b * S + warp;
+                        const uint32_t pre = valid ? (uint32_t)*c : 0u;
+                        __syncwarp();
+                        if (valid && (peers & lt_mask) == 0) *c = (uint16_t)(pre + (uint32_t)__popc(peers));
+                        __syncwarp();
+                        if (valid) packed[s] = b | ((pre + (uint32_t)__popc(peers & lt_mask)) << 10);
+                    }
+                }
+                compute_sync();  // A
+
+                // bookkeeping: one lane per bucket; the (bucket, warp) counts become offsets from
+                // the start of the bucket's current chunk (below Bs: the staged chunk)
+                {
+                    const int64_t e_rd = (int64_t)R + round - delta;  // elements read through this round
+                    const uint32_t e_end = min(e_rd < (int64_t)r ? (uint32_t)e_rd : r, avail);
+                    const uint32_t F = min(H, b_pow2 ? e_end >> b_shift : a.fdB.div(e_end));
+                    for (uint32_t b0 = warp * 32u; b0 < k; b0 += kComputeThreads) {
+                        const uint32_t b = b0 + lane;
+                        const bool mine = b < k;
+                        const uint32_t cur = mine ? run[b] : 0u;
+                        const uint32_t fill = bs_pow2 ? cur & (Bs - 1u) : cur % Bs;
+                        uint32_t acc = fill;
+                        if (mine) {
+                            uint16_t* col = tbl + b * S;
+                            if constexpr (KB > 0) {
+#pragma unroll
+                                for (uint32_t j = 0; j < cls_nwr(KC, W); ++j) {
+                                    const uint32_t c = col[j];
+                                    col[j] = (uint16_t)acc;
+                                    acc += c;
+                                }
+                            } else {
+                                for (uint32_t j = 0; j < nwr; ++j) {
+                                    const uint32_t c = col[j];
+                                    col[j] = (uint16_t)acc;
+                                    acc += c;
+                                }
+                            }
+                        }
+                        const uint32_t t = acc - fill, nr = cur + t;
+                        const uint32_t c0 = bs_pow2 ? cur >> bs_shift : cur / Bs;
+                        const uint32_t c1 = bs_pow2 ? nr >> bs_shift : nr / Bs;
+                        const bool moves = mine && c1 > c0;  // a chunk completes: blocks receive data
+                        uint32_t jlo = 0, jhi = 0, ob = kNone, jn = 0, nb = 0;
+                        uint64_t oloc = 0;
+                        if (moves) {
+                            jlo = c0 / cpb;
+                            jhi = (c1 - 1u) / cpb;
+                            ob = oblk[b];
+                            oloc = optr[b];
+                            jn = ob == jlo ? jlo + 1u : jlo;
+                            nb = jhi + 1u - jn;
+                        }
+                        uint32_t ex = nb;
+#pragma unroll
+                        for (uint32_t d = 1; d < 32u; d <<= 1) {
+                            const uint32_t y = __shfl_up_sync(0xffffffffu, ex, d);
+                            if (lane >= d) ex += y;
+                        }
+                        const uint32_t wtotal = __shfl_sync(0xffffffffu, ex, 31);
+                        ex -= nb;
+                        // whole blocks staged: completed blocks never outrun the read elements, so
+                        // the frontier binds only past H (wrap piece) and a plain add is exact;
+                        // chunks: a block is placed at its first chunk, so claim no slot past F
+                        uint32_t hb0 = 0, lim = F;
+                        if (lane == 0 && wtotal) {
+                            if (cpb == 1) {
+                                hb0 = atomicAdd(&ms.home_next, wtotal);
+                            } else {
+                                uint32_t old = *reinterpret_cast<volatile uint32_t*>(&ms.home_next), tk = 0;
+                                for (;;) {
+                                    tk = old < F ? min(wtotal, F - old) : 0u;
+                                    if (tk == 0) break;
+                                    const uint32_t prev = atomicCAS(&ms.home_next, old, old + tk);
+                                    if (prev == old) break;
+                                    old = prev;
+                                }
+                                hb0 = old;
+                                lim = old + tk;
+                            }
+                        }
+                        hb0 = __shfl_sync(0xffffffffu, hb0, 0);
+                        lim = __shfl_sync(0xffffffffu, lim, 0);
+                        const unsigned fl_mask = __ballot_sync(0xffffffffu, moves);
+                        uint32_t fl0 = 0;
+                        if (lane == 0 && fl_mask) fl0 = atomicAdd(&ms.nflush[par], (uint32_t)__popc(fl_mask));
+                        fl0 = __shfl_sync(0xffffffffu, fl0, 0);
+                        if (mine && t) {
+                            rb[b] = cur;
+                            run[b] = nr;
+                        }
+                        if (moves) {
+                            const uint32_t hb = hb0 + ex;
+                            const uint32_t tk = lim > hb ? min(nb, lim - hb) : 0u;
+                            uint64_t pb = 0;
+                            if (nb > tk) {
+                                const uint64_t need = (uint64_t)(nb - tk) * B;
+                                const uint64_t alloc = (need + a.pool_align - 1) / a.pool_align * a.pool_align;
+                                pb = atomicAdd((unsigned long long*)a.pool_used, (unsigned long long)alloc);
+                                if (pb + need > a.pool_cap) report(a.status, RIP_EWORKSPACE, 0x6202, pb);
+                            }
+                            jnew[b] = jn;
+                            take[b] = tk;
+                            hbase[b] = hb;
+                            pbase[b] = pb;
+                            auto locf = [&](uint32_t j) -> uint64_t {
+                                if (j == ob) return oloc;
+                                const uint32_t x = j - jn;
+                                if (x < tk) return alo + (uint64_t)(hb + x) * B;
+                                return kLocPool | (pb + (uint64_t)(x - tk) * B);
+                            };
+                            const uint64_t l0 = locf(jlo);
+                            jloc[b] = l0;
+                            // the staged chunk c0 completes: its flush entry
+                            flist[par * k + fl0 + (uint32_t)__popc(fl_mask & lt_mask)] =
+                                (l0 + (uint64_t)(c0 % cpb) * Bs) | ((uint64_t)b << 48);
+                            // blocks completed this round: slot words (home) or demoted records (pool)
+                            const uint32_t jc0 = b_pow2 ? cur >> b_shift : a.fdB.div(cur);
+                            const uint32_t jc1 = b_pow2 ? nr >> b_shift : a.fdB.div(nr);
+                            for (uint32_t j = jc0; j < jc1; ++j) {
+                                if (j >= (1u << kBlkBits)) report(a.status, RIP_EINVAL, 0x6203, j);
+                                const uint64_t l = locf(j);
+                                if (!(l & kLocPool)) {
+                                    const uint32_t h = b_pow2 ? (uint32_t)((l - alo) >> b_shift)
+                                                              : a.fdB.div((uint32_t)(l - alo));
+                                    a.words[hs0 + h] = kWordOcc | (b << kBlkBits) | j;
+                                } else {
+                                    if ((l & ~kLocPool) + B > a.pool_cap) continue;  // allocation failure, reported
+                                    const uint32_t rec = atomicAdd(&a.counters[2], 1u);
+                                    if (rec < a.dem_cap)
+                                        a.dem[rec] = DemRec{tr.sp, tile, b, j, l & ~kLocPool};
+                                    else
+                                        report(a.status, RIP_EWORKSPACE, 0x6204, rec);
+                                }
+                            }
+                            if ((uint64_t)(jhi + 1u) * B > nr) {
+                                oblk[b] = jhi;
+                                optr[b] = locf(jhi);
+                            } else {
+                                oblk[b] = kNone;
+                            }
+                        }
+                    }
+                }
+                // this round's input is loaded and the previous round's chunks are read out
+                if (tid == 0) {
+                    if (!mbar_wait(&ms.full[gr % nbuf], (gr / nbuf) & 1u)) {
+                        report(a.status, RIP_ETIMEOUT, 0x6207, gr);
+                        ms.fail = 1;
+                    }
+                    if (!mbar_wait(&ms.stage_free, (sfc + rr) & 1u)) {
+                        report(a.status, RIP_ETIMEOUT, 0x6209, gr);
+                        ms.fail = 1;
+                    }
+                }
+                compute_sync();  // B
+                if (ms.fail) {
+                    if (tid == 0) mbar_arrive(&ms.flush_ready);  // lets the I/O warp see the failure
+                    break;
+                }
+
+                // place: carried elements of the previous round, then this round's
+                {
+                    const T* cb = bufs + (size_t)carried_buf * g.bufstride;
+#pragma unroll
+                    for (uint32_t s = 0; s < 4; ++s) {
+                        const uint32_t cv = carried[s];
+                        if (cv == kNone) continue;
+                        const uint32_t bi = cv & 0x1FFFu, b = (cv >> 13) & 0x3FFu, pos = cv >> 23;
+                        stage[(size_t)b * Bs + pos] = cb[bi];
+                    }
+                }
+                const T* vb = bufs + (size_t)(gr % nbuf) * g.bufstride;
+                const uint32_t sh = shift_of(rr);
+#pragma unroll
+                for (uint32_t s = 0; s < 4; ++s) {
+                    const uint32_t p = packed[s];
+                    carried[s] = kNone;
+                    if (p == kNone) continue;
+                    const uint32_t b = p & 0x3FFu, rk = p >> 10;
+                    const uint32_t x = tbl[b * S + warp] + rk;  // offset from the current chunk's start
+                    const uint32_t bi = warp * 128u + 32u * s + lane + sh;
+                    if (x < Bs) {
+                        stage[(size_t)b * Bs + x] = vb[bi];
+                        continue;
+                    }
+                    const uint32_t qx = bs_pow2 ? x >> bs_shift : x / Bs;  // chunks past the current one
+                    const uint32_t pos = x - qx * Bs;
+                    const uint32_t rbb = rb[b], run_b = run[b];
+                    const uint32_t c0 = bs_pow2 ? rbb >> bs_shift : rbb / Bs;
+                    const uint32_t c1 = bs_pow2 ? run_b >> bs_shift : run_b / Bs;
+                    const uint32_t c = c0 + qx;
+                    if (c < c1) {  // the whole chunk lies in this round: straight to its block
+                        const uint32_t j = c / cpb, jlo = c0 / cpb;
+                        uint64_t l;
+                        if (j == jlo) {
+                            l = jloc[b];
+                        } else {
+                            const uint32_t xj = j - jnew[b], tk = take[b];
+                            l = xj < tk ? alo + (uint64_t)(hbase[b] + xj) * B
+                                        : kLocPool | (pbase[b] + (uint64_t)(xj - tk) * B);
+                        }
+                        if ((l & kLocPool) && (l & ~kLocPool) + B > a.pool_cap) continue;  // reported at allocation
+                        loc_ptr(l + (uint64_t)(c % cpb) * Bs)[pos] = vb[bi];
+                    } else {
+                        carried[s] = bi | (b << 13) | (pos << 23);
+                    }
+                }
+                carried_buf = gr % nbuf;
+                if (flush_vec) fence_proxy_async_smem();  // staged elements are read by bulk stores
+                // the warp's column of the table is read only by the warp itself: clear it
+                __syncwarp();
+                if (warp < nwr)
+                    for (uint32_t b = lane; b < k; b += 32u) tbl[b * S + warp] = 0;
+                compute_sync();  // C
+                if (tid == 0) mbar_arrive(&ms.flush_ready);
+            }
+            // end of the tile: the last chunks are read out, then the carried elements
+            if (!ms.fail) {
+                if (tid == 0 && !mbar_wait(&ms.stage_free, (sfc + nrounds) & 1u)) {
+                    report(a.status, RIP_ETIMEOUT, 0x620A, nrounds);
+                    ms.fail = 1;
+                }
+                compute_sync();
+                const T* cb = bufs + (size_t)carried_buf * g.bufstride;
+#pragma unroll
+                for (uint32_t s = 0; s < 4; ++s) {
+                    const uint32_t cv = carried[s];
+                    if (cv == kNone) continue;
+                    const uint32_t bi = cv & 0x1FFFu, b = (cv >> 13) & 0x3FFu, pos = cv >> 23;
+                    stage[(size_t)b * Bs + pos] = cb[bi];
+                }
+            }
+        }
+        grc += nrounds;
+        sfc += nrounds + 1u;
+        frc += nrounds;
+        __syncthreads();
+        if (ms.fail) break;  // a copy or a hand-off did not arrive: reported, the level's output is void
+        {
+            // tails of every bucket -> pool, in bucket order; k <= 2 * blockDim.x
+            const uint32_t i0 = 2 * tid, i1 = 2 * tid + 1;
+            const uint32_t r0 = i0 < k ? a.fdB.mod(run[i0]) : 0, r1 = i1 < k ? a.fdB.mod(run[i1]) : 0;
+            uint32_t total;
+            const uint32_t ex = block_exclusive_scan<uint32_t>(r0 + r1, ms.scan, &total);
+            if (i0 < k) jnew[i0] = ex;  // reused: tail offset of the bucket
+            if (i1 < k) jnew[i1] = ex + r0;
+            if (tid == 0) {
+                const uint64_t alloc = ((uint64_t)total + a.pool_align - 1) / a.pool_align * a.pool_align;
+                const uint64_t pb = atomicAdd((unsigned long long*)a.pool_used, (unsigned long long)alloc);
+                if (pb + total > a.pool_cap) report(a.status, RIP_EWORKSPACE, 0x6205, pb);
+                ms.pool_base = pb;
+            }
+            __syncthreads();
+            const uint64_t pb = ms.pool_base;
+            const uint32_t nwarps = blockDim.x >> 5;
+            for (uint32_t b = warp; b < k; b += nwarps) {
+                const uint32_t nr = run[b];
+                const uint32_t Rt = a.fdB.mod(nr);
+                const uint32_t in_stage = bs_pow2 ? nr & (Bs - 1u) : nr % Bs;
+                const uint32_t in_block = Rt - in_stage;  // elements already in the open block
+                const uint64_t ol = optr[b];
+                const bool ob_ok = !in_block || !(ol & kLocPool) || (ol & ~kLocPool) + B <= a.pool_cap;
+                if (pb + total <= a.pool_cap && ob_ok) {
+                    const T* obp = in_block ? loc_ptr(ol) : nullptr;
+                    for (uint32_t j = lane; j < Rt; j += 32u)
+                        pool[pb + jnew[b] + j] = j < in_block ? obp[j] : stage[(size_t)b * Bs + (j - in_block)];
+                }
+                if (lane == 0 && oblk[b] != kNone && !(optr[b] & kLocPool)) {
+                    // an open block in a home slot held a part of the tail only: that slot is empty
+                    const uint64_t l = optr[b];
+                    const uint32_t h = b_pow2 ? (uint32_t)((l - alo) >> b_shift) : a.fdB.div((uint32_t)(l - alo));
+                    a.words[hs0 + h] = 0u;
+                }
+            }
+            for (uint32_t b = tid; b < k; b += blockDim.x) a.C[(uint64_t)tile * k + b] = run[b];
+            const uint32_t used = min(ms.home_next, H);
+            if (tid == 0) a.tinfo[tile] = TileInfo{hs0, pb, used, H};
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace
+
+bool classify_config(uint32_t k, uint32_t B, uint32_t w, ClsCfg* out) {
+    if (k < 2 || k > kMaxK || (k & (k - 1)) || B < 1) return false;
+    ClsCfg c{};
+    c.nwr = cls_nwr(k, w);
+    c.S = cls_stride(k, w);
+    c.round = c.nwr * 128u;
+    c.q = w >= 16 ? 1u : 16u / w;
+    c.bufstride = (c.round + c.q + 15u) / 16u * 16u;  // elements; keeps every buffer 16-byte aligned
+    auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+    size_t off = a16(sizeof(ClsMisc));
+    c.off_tbl = (uint32_t)off;
+    off = a16(off + (size_t)k * c.S * 2);
+    c.off_u32 = (uint32_t)off;
+    off = a16(off + (size_t)k * 6 * 4);
+    c.off_u64 = (uint32_t)off;
+    off = a16(off + (size_t)k * 3 * 8);
+    c.off_flist = (uint32_t)off;
+    off = a16(off + (size_t)k * 2 * 8);
+    const size_t fixed = off;
+    const size_t buf_bytes = a16((size_t)c.bufstride * w);
+    uint32_t best_d = 0, best_nbuf = 0;
+    for (uint32_t nbuf = 3; nbuf >= 2; --nbuf) {
+        if (fixed + nbuf * buf_bytes >= kSmemOptin) continue;
+        const size_t rem = kSmemOptin - fixed - nbuf * buf_bytes;
+        uint32_t d = 0;
+        for (uint32_t x = std::min<uint32_t>(B, 512u); x >= 1; --x)
+            if (B % x == 0 && (size_t)k * x * w <= rem) {
+                d = x;
+                break;
+            }
+        // prefer whole blocks in shared memory (no pool blocks for open blocks), then more buffers
+        if (d > best_d) {
+            best_d = d;
+            best_nbuf = nbuf;
+        }
+    }
+    if (!best_d) return false;
+    c.Bs = best_d;
+    c.cpb = B / best_d;
+    c.nbuf = best_nbuf;
+    c.off_stage = (uint32_t)fixed;
+    c.off_buf = (uint32_t)a16(fixed + (size_t)k * c.Bs * w);
+    c.bytes = (uint32_t)(c.off_buf + c.nbuf * buf_bytes);
+    if (c.bytes > kSmemOptin) return false;
+    *out = c;
+    return true;
+}
+
+template <int W, int KB>
+static cudaError_t launch_cls(const LevelArgs& a, uint32_t num_sms, cudaStream_t s) {
+    const int smem = (int)a.cls.bytes;
+    cudaError_t err = cudaFuncSetAttribute(classify_kernel<W, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (err != cudaSuccess) return err;
+    classify_kernel<W, KB><<<num_sms, kClassifyThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int W>
+static cudaError_t launch_cls_w(const LevelArgs& a, uint32_t num_sms, cudaStream_t s) {
+    switch (a.k) {  // the common bucket counts get kernels with k fixed at compile time
+        case 64: return launch_cls<W, 6>(a, num_sms, s);
+        case 256: return launch_cls<W, 8>(a, num_sms, s);
+        case 1024: return launch_cls<W, 10>(a, num_sms, s);
+        default: return launch_cls<W, 0>(a, num_sms, s);
+    }
+}
+
+cudaError_t launch_classify(const LevelArgs& a, uint32_t w, uint32_t num_sms, cudaStream_t s) {
+    ProfScope p("classify", s);
+    switch (w) {
+        case 4: return launch_cls_w<4>(a, num_sms, s);
+        case 8: return launch_cls_w<8>(a, num_sms, s);
+        default: return launch_cls_w<16>(a, num_sms, s);
+    }
+}
+
+}  // namespace rip

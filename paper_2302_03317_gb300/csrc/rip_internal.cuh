@@ -12,7 +12,6 @@ constexpr uint32_t kSmallTbl = 4096;      // (ranking warp, bucket) entries
 constexpr uint32_t kSmallStack = 256;     // pending scatter ranges inside one subproblem
 constexpr uint32_t kMediumMaxM = 49152;   // largest subproblem finished on one SM
 constexpr uint32_t kClassifyThreads = 1024;
-constexpr uint32_t kClsTbl = 8192;   // (ranking warp, bucket) entries: 32 warps x 256
 constexpr uint32_t kPermuteThreads = 256;
 constexpr uint32_t kGroup = 8;            // lanes moving one block in the permutation
 constexpr size_t kSmemOptin = 232448;     // dynamic shared memory per block on sm_100/103
@@ -75,6 +74,19 @@ struct Lists {
     uint32_t bigfy_cap;
 };
 
+// Shared-memory geometry of the classify kernel for one (k, B, w), chosen on the host.
+struct ClsCfg {
+    uint32_t Bs;         // elements per shared-memory chunk (divides B; == B: whole blocks staged)
+    uint32_t cpb;        // chunks per block
+    uint32_t nwr;        // ranking warps (the (bucket, warp) table holds k * nwr counters)
+    uint32_t S;          // table stride per bucket (odd, > nwr: conflict-free columns)
+    uint32_t round;      // positions per round (nwr * 128)
+    uint32_t q;          // elements per 16 bytes
+    uint32_t nbuf;       // input buffers (2 or 3)
+    uint32_t bufstride;  // elements per input buffer
+    uint32_t off_tbl, off_u32, off_u64, off_flist, off_stage, off_buf, bytes;
+};
+
 struct LevelArgs {
     const ArrayDesc* arrays;
     DevPlan plan;
@@ -120,6 +132,7 @@ struct LevelArgs {
     ParkRec* parks;
     uint32_t park_cap;
     uint32_t park_after;  // chain steps before a carried block is parked
+    ClsCfg cls;
 };
 
 struct SmallArgs {
@@ -163,8 +176,11 @@ size_t small_fixed_smem();
 size_t small_smem_bytes(uint64_t m, uint32_t w, bool medium);
 cudaError_t launch_small(const SmallArgs& args, uint32_t w, size_t smem, uint32_t grid, cudaStream_t stream);
 
+// rip_classify.cu
+bool classify_config(uint32_t k, uint32_t B, uint32_t w, ClsCfg* out);
+cudaError_t launch_classify(const LevelArgs& a, uint32_t w, uint32_t num_sms, cudaStream_t s);
+
 // rip_level.cu
-size_t classify_smem_bytes(uint32_t k, uint32_t B, uint32_t w);
 size_t permute_smem_bytes(uint32_t B, uint32_t w);
 cudaError_t launch_init(const InitArgs& a, cudaStream_t s);
 cudaError_t launch_level(const LevelArgs& a, uint32_t w, uint32_t num_sms, cudaStream_t s, uint32_t* launches);

@@ -5,11 +5,11 @@
 // becomes a contiguous region) for every subproblem too large for one SM:
 //
 //  tiles     build the level's tile list (T elements per tile, per subproblem)
-//  classify  one CTA streams one tile: Philox bucket draws, stable ranks per
-//            bucket (warp match_any + per-warp counts), B-element bucket
-//            buffers in shared memory; every completed block is written back
-//            into the tile's own, already-read front ("home slots"); the
-//            partial buffers (the tails) go to a small pool
+//  classify  one CTA streams one tile (rip_classify.cu): Philox bucket
+//            draws, stable ranks per bucket, chunks staged in shared memory;
+//            every completed block is written back into the tile's own,
+//            already-read front ("home slots") or a small pool; the partial
+//            streams (the tails) go to the pool
 //  scan      per subproblem: bucket sizes, region starts, per-(tile, bucket)
 //            prefix of full blocks and tails, child descriptors and rotations
 //  resolve   turn each home slot's (bucket, block) into its destination slot
@@ -141,297 +141,6 @@ __global__ void tiles_kernel(LevelArgs a) {
     }
 }
 
-// ------------------------------------------------------------------ classify
-
-struct ClsShared {
-    uint32_t run[kMaxK];      // bucket elements seen in this tile
-    uint32_t newrun[kMaxK];   // ... after the current round
-    uint32_t hsb[kMaxK];      // home index of the first block completing this round
-    uint32_t binfo[kMaxK];    // per bucket this round: (run mod B) | (blocks completing) << 16
-    uint32_t dfirst[kMaxK];   // first home index that is demoted, per bucket (this round)
-    uint64_t dbase[kMaxK];    // pool offset of that demoted block
-    uint32_t tbl[kClsTbl];    // (ranking warp, bucket) counts of the round
-    uint32_t mask[kClsTbl];   // (ranking warp, bucket) lanes of the current step, zero between steps
-    uint16_t flist[kMaxK];    // buckets whose buffered block completes this round
-    uint32_t scan[32];
-    uint32_t nflush;
-    uint32_t home_next;
-    uint32_t tile;
-    uint32_t pad;
-    uint64_t pool_base;
-};
-
-// Element order inside a tile is its position order.  A round covers nwr * G
-// groups of 128 positions (aligned to multiples of four in the global position
-// space); ranking warp w owns groups w*G .. w*G+G-1 of the round, lane l of
-// step s holds position 4 Qg + 32 s + l.  Stable ranks: match_any inside a
-// step, a per-warp running count per bucket across the warp's steps, and one
-// exclusive prefix over the warps per bucket and round.
-template <int W, int G>
-__global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs a) {
-    using T = typename Elem<W>::T;
-    constexpr uint32_t E = 4 * G;  // elements per lane per round
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    ClsShared& sh = *reinterpret_cast<ClsShared*>(smem_raw);
-    T* buf = reinterpret_cast<T*>(smem_raw + ((sizeof(ClsShared) + 15) & ~size_t(15)));
-    const uint32_t k = a.k, B = a.B, L = a.level;
-    const uint32_t kbits = log2_pow2(k);
-    const bool bpow2 = (B & (B - 1u)) == 0;
-    const uint32_t bshift = log2_pow2(B);
-    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    const uint32_t nwarps = blockDim.x >> 5;
-    const uint32_t nwr = min(nwarps, kClsTbl / k);
-    const uint32_t round = nwr * 128u * G;
-    const uint32_t ntiles = a.counters[0];
-    const uint32_t lt_mask = (1u << lane) - 1u;
-
-    for (;;) {
-        if (tid == 0) sh.tile = atomicAdd(&a.counters[1], 1u);
-        __syncthreads();
-        const uint32_t tile = sh.tile;
-        if (tile >= ntiles) break;
-        const TileRef tr = a.tiles[tile];
-        const Sub S = a.big[tr.sp];
-        const ArrayDesc ad = a.arrays[S.arr];
-        T* base = reinterpret_cast<T*>(ad.data);
-        const PhiloxKey pk = make_key(ad.seed);
-        const uint64_t lo = (uint64_t)tr.t * a.T;
-        const uint32_t r = (uint32_t)(min(lo + a.T, S.m) - lo);
-        const uint64_t alo = S.o + S.eps + lo;  // physical start of the tile's aligned piece
-        const uint64_t avail = S.m > S.eps + lo ? min((uint64_t)r, S.m - S.eps - lo) : 0;
-        const uint32_t H = (uint32_t)(avail / B);
-        const uint64_t hs0 = ad.slot_base + alo / B;
-        const uint64_t P0 = S.o + lo;           // logical global position of the tile's first element
-        const uint32_t delta = (uint32_t)(P0 & 3u);
-        const uint64_t Q0 = P0 >> 2;
-        const uint32_t rv = r + delta;          // positions covered, counted from 4*Q0
-        if (alo % B != 0 && tid == 0) report(a.status, RIP_EINTERNAL, 0x6201, alo);
-
-        // Slots of this level's grid inside the leading wrap piece [o, o+eps) lie in the
-        // region but in no tile's home range (only when B is smaller than the parent's):
-        // mark them empty so the permutation may fill them.
-        if (tr.t == 0 && S.eps >= B) {
-            const uint64_t first = (S.o + B - 1) / B, last = (S.o + S.eps) / B;
-            for (uint64_t g = first + tid; g < last; g += blockDim.x) a.words[ad.slot_base + g] = 0u;
-        }
-        for (uint32_t b = tid; b < k; b += blockDim.x) sh.run[b] = 0;
-        for (uint32_t j = tid; j < nwr * k; j += blockDim.x) {
-            sh.tbl[j] = 0;
-            sh.mask[j] = 0;
-        }
-        if (tid == 0) {
-            sh.home_next = 0;
-            sh.nflush = 0;
-        }
-        // elements [0, avail) of the tile are contiguous at base + alo; the rest (the
-        // rotation's wrap piece) goes through phys_index
-        const T* tile_ptr = base + alo;
-        auto load_round = [&](T (&dst)[E], uint32_t Rv) {
-            const uint32_t v0 = Rv + warp * G * 128u + lane;  // position of element e = 0
-            if (v0 >= delta && Rv + (warp * G + G) * 128u <= avail + delta) {
-                const T* p = tile_ptr + (v0 - delta);
-#pragma unroll
-                for (uint32_t e = 0; e < E; ++e) dst[e] = p[(e / 4) * 128u + 32u * (e % 4)];
-            } else {
-#pragma unroll
-                for (uint32_t e = 0; e < E; ++e) {
-                    const uint32_t v = v0 + (e / 4) * 128u + 32u * (e % 4);
-                    if (v >= delta && v - delta < r) dst[e] = base[phys_index(S, lo + (v - delta))];
-                }
-            }
-        };
-        T val[E], nxt[E];
-        if (warp < nwr) load_round(nxt, 0);
-        __syncthreads();
-
-        for (uint32_t R = 0; R < rv; R += round) {
-            uint32_t bb[E], rk[E];
-            if (warp < nwr) {
-#pragma unroll
-                for (uint32_t e = 0; e < E; ++e) val[e] = nxt[e];
-                if (R + round < rv) load_round(nxt, R + round);
-                uint4 words[G];
-#pragma unroll
-                for (uint32_t g = 0; g < G; ++g)
-                    words[g] = group_philox(pk, L, S.o, Q0 + (R >> 2) + (warp * G + g) * 32u);
-#pragma unroll
-                for (uint32_t e = 0; e < E; ++e) {
-                    const uint32_t v = R + (warp * G + e / 4) * 128u + 32u * (e % 4) + lane;
-                    const bool valid = v >= delta && v - delta < r;
-                    const uint32_t b = bucket_of(group_step_word(words[e / 4], e % 4), k);
-                    // lanes of this step with the same bucket: OR the lane bits into the warp's row
-                    uint32_t* mrow = sh.mask + warp * k;
-                    if (valid) atomicOr(&mrow[b], 1u << lane);
-                    __syncwarp();
-                    const uint32_t peers = valid ? mrow[b] : 0u;
-                    const uint32_t leader = valid ? (uint32_t)(__ffs(peers) - 1) : lane;
-                    uint32_t pre = 0;
-                    // only this warp touches row `warp`: the returned count is the one before this step
-                    if (valid && lane == leader) pre = atomicAdd(&sh.tbl[warp * k + b], (uint32_t)__popc(peers));
-                    __syncwarp();
-                    if (valid && lane == leader) mrow[b] = 0u;
-                    __syncwarp();
-                    pre = __shfl_sync(0xffffffffu, pre, (int)leader);
-                    bb[e] = valid ? b : 0xffffffffu;
-                    rk[e] = pre + __popc(peers & lt_mask);
-                }
-            }
-            __syncthreads();
-
-            // per bucket: exclusive prefix over the ranking warps (in place), completed
-            // blocks, home slots, demotion
-            for (uint32_t b = tid; b < k; b += blockDim.x) {
-                uint32_t tot = 0;
-                for (uint32_t w = 0; w < nwr; ++w) tot += sh.tbl[w * k + b];
-                const uint32_t rb = sh.run[b], nr = rb + tot;
-                sh.newrun[b] = nr;
-                const uint32_t cb = a.fdB.div(rb), eb = a.fdB.div(nr);
-                const uint32_t rem = rb - cb * B;
-                sh.binfo[b] = rem | ((eb - cb) << 16);
-                // per (warp, bucket): offset of the warp's first element in the bucket's
-                // current partial block (< 2^16), and the number of completing blocks
-                uint32_t acc = rem;
-                for (uint32_t w = 0; w < nwr; ++w) {
-                    const uint32_t c = sh.tbl[w * k + b];
-                    sh.tbl[w * k + b] = acc | ((eb - cb) << 16);
-                    acc += c;
-                }
-                if (eb > cb) {
-                    const uint32_t nb = eb - cb;
-                    const uint32_t hs = atomicAdd(&sh.home_next, nb);
-                    sh.hsb[b] = hs;
-                    const uint32_t first_dem = max(hs, H);
-                    const uint32_t ndem = hs + nb > first_dem ? hs + nb - first_dem : 0;
-                    uint64_t pool_off = 0;
-                    if (ndem) {
-                        // pool allocations stay 16-byte aligned: blocks are copied with 16-byte vectors
-                        const uint64_t alloc = ((uint64_t)ndem * B + a.pool_align - 1) / a.pool_align * a.pool_align;
-                        pool_off = atomicAdd((unsigned long long*)a.pool_used, (unsigned long long)alloc);
-                        if (pool_off + (uint64_t)ndem * B > a.pool_cap) report(a.status, RIP_EWORKSPACE, 0x6202, pool_off);
-                        sh.dfirst[b] = first_dem;
-                        sh.dbase[b] = pool_off;
-                    }
-                    for (uint32_t j = 0; j < nb; ++j) {
-                        const uint32_t h = hs + j, blk = cb + j;
-                        if (blk >= (1u << kBlkBits)) report(a.status, RIP_EINVAL, 0x6203, blk);
-                        if (h < H) {
-                            a.words[hs0 + h] = kWordOcc | (b << kBlkBits) | blk;
-                        } else {
-                            const uint32_t rec = atomicAdd(&a.counters[2], 1u);
-                            if (rec < a.dem_cap)
-                                a.dem[rec] = DemRec{tr.sp, tile, b, blk, pool_off + (uint64_t)(h - first_dem) * B};
-                            else
-                                report(a.status, RIP_EWORKSPACE, 0x6204, rec);
-                        }
-                    }
-                    if (rem != 0) sh.flist[atomicAdd(&sh.nflush, 1u)] = (uint16_t)b;
-                }
-            }
-            __syncthreads();
-
-            // phase 1: elements of blocks completing in this round
-            if (warp < nwr) {
-#pragma unroll
-                for (uint32_t e = 0; e < E; ++e) {
-                    const uint32_t b = bb[e];
-                    if (b == 0xffffffffu) continue;
-                    // offset inside the bucket's current partial block, counted from its start
-                    const uint32_t we = sh.tbl[warp * k + b];
-                    const uint32_t local = (we & 0xFFFFu) + rk[e];
-                    const uint32_t q = bpow2 ? local >> bshift : a.fdB.div(local);
-                    const uint32_t pos = local - q * B;
-                    rk[e] = pos;
-                    if (q < (we >> 16)) {
-                        if (q == 0 && (sh.binfo[b] & 0xFFFFu) != 0) {
-                            buf[b * B + pos] = val[e];
-                        } else {
-                            const uint32_t h = sh.hsb[b] + q;
-                            const uint64_t poff = sh.dbase[b] + (uint64_t)(h - sh.dfirst[b]) * B;
-                            if (h >= H && poff + B > a.pool_cap) continue;  // reported at allocation
-                            T* dst = h < H ? base + alo + (uint64_t)h * B : reinterpret_cast<T*>(a.pool) + poff;
-                            dst[pos] = val[e];
-                        }
-                        bb[e] = 0xffffffffu;  // placed
-                    }
-                }
-            }
-            __syncthreads();
-
-            // flush the buffered blocks that completed
-            {
-                const uint32_t nf = sh.nflush;
-                for (uint32_t f = warp; f < nf; f += nwarps) {
-                    const uint32_t b = sh.flist[f];
-                    const uint32_t h = sh.hsb[b];
-                    const uint64_t poff = sh.dbase[b] + (uint64_t)(h - sh.dfirst[b]) * B;
-                    if (h >= H && poff + B > a.pool_cap) continue;  // reported at allocation
-                    T* dst = h < H ? base + alo + (uint64_t)h * B : reinterpret_cast<T*>(a.pool) + poff;
-                    const T* src = buf + b * B;
-                    if (a.vec16 && W < 16 && (reinterpret_cast<uintptr_t>(dst) & 15u)) {
-                        if (lane == 0) report(a.status, RIP_EINTERNAL, 0x6206, reinterpret_cast<uintptr_t>(dst));
-                        continue;
-                    }
-                    if (a.vec16 && W < 16) {
-                        const uint32_t units = B * W / 16u;
-                        for (uint32_t u = lane; u < units; u += 32u)
-                            reinterpret_cast<uint4*>(dst)[u] = reinterpret_cast<const uint4*>(src)[u];
-                    } else {
-                        for (uint32_t u = lane; u < B; u += 32u) dst[u] = src[u];
-                    }
-                }
-            }
-            __syncthreads();
-
-            // phase 2: elements that start the next partial block
-            if (warp < nwr) {
-#pragma unroll
-                for (uint32_t e = 0; e < E; ++e) {
-                    const uint32_t b = bb[e];
-                    if (b == 0xffffffffu) continue;
-                    buf[b * B + rk[e]] = val[e];
-                }
-            }
-            for (uint32_t b = tid; b < k; b += blockDim.x) {
-                sh.run[b] = sh.newrun[b];
-                for (uint32_t w = 0; w < nwr; ++w) sh.tbl[w * k + b] = 0;
-            }
-            if (tid == 0) sh.nflush = 0;
-            __syncthreads();
-        }
-
-        // tails of every bucket -> pool; counts and tile info
-        {
-            // k <= kMaxK <= 2 * blockDim.x: two buckets per thread
-            const uint32_t i0 = 2 * tid, i1 = 2 * tid + 1;
-            const uint32_t r0 = i0 < k ? a.fdB.mod(sh.run[i0]) : 0, r1 = i1 < k ? a.fdB.mod(sh.run[i1]) : 0;
-            uint32_t total;
-            const uint32_t ex = block_exclusive_scan<uint32_t>(r0 + r1, sh.scan, &total);
-            if (i0 < k) sh.hsb[i0] = ex;
-            if (i1 < k) sh.hsb[i1] = ex + r0;
-            if (tid == 0) {
-                const uint64_t alloc = ((uint64_t)total + a.pool_align - 1) / a.pool_align * a.pool_align;
-                const uint64_t pb = atomicAdd((unsigned long long*)a.pool_used, (unsigned long long)alloc);
-                if (pb + total > a.pool_cap) report(a.status, RIP_EWORKSPACE, 0x6205, pb);
-                sh.pool_base = pb;
-            }
-            __syncthreads();
-            const uint64_t pb = sh.pool_base;
-            if (pb + total <= a.pool_cap) {
-                T* pool = reinterpret_cast<T*>(a.pool);
-                for (uint32_t b = warp; b < k; b += nwarps) {
-                    const uint32_t R = a.fdB.mod(sh.run[b]);
-                    for (uint32_t j = lane; j < R; j += 32u) pool[pb + sh.hsb[b] + j] = buf[b * B + j];
-                }
-            }
-            for (uint32_t b = tid; b < k; b += blockDim.x) a.C[(uint64_t)tile * k + b] = sh.run[b];
-            const uint32_t used = min(sh.home_next, H);
-            for (uint32_t h = used + tid; h < H; h += blockDim.x) a.words[hs0 + h] = 0u;
-            if (tid == 0) a.tinfo[tile] = TileInfo{hs0, pb, used, H};
-            __syncthreads();
-        }
-    }
-}
-
 // ------------------------------------------------------------------ scan
 
 __global__ void scan_kernel(LevelArgs a, uint32_t small_max_m) {
@@ -505,6 +214,7 @@ __global__ void resolve_kernel(LevelArgs a) {
         const TileInfo ti = a.tinfo[tile];
         for (uint32_t h = threadIdx.x; h < ti.home_used; h += blockDim.x) {
             const uint32_t w = a.words[ti.hs0 + h];
+            if ((w & (kWordOcc | kWordTaken)) != kWordOcc) continue;  // empty: held a part of a tail only
             const uint32_t b = (w >> kBlkBits) & (kMaxK - 1u);
             const uint32_t blk = w & ((1u << kBlkBits) - 1u);
             const ChildInfo ci = a.child[(uint64_t)tr.sp * k + b];
@@ -860,10 +570,6 @@ __global__ void bigfy_kernel(const Sub* list, const uint32_t* count, uint32_t ca
 
 }  // namespace
 
-size_t classify_smem_bytes(uint32_t k, uint32_t B, uint32_t w) {
-    return ((sizeof(ClsShared) + 15) & ~size_t(15)) + (size_t)k * B * w;
-}
-
 size_t permute_smem_bytes(uint32_t B, uint32_t w) {
     return (size_t)(kPermuteThreads / kGroup) * B * w;
 }
@@ -876,19 +582,13 @@ cudaError_t launch_init(const InitArgs& a, cudaStream_t s) {
 
 template <int W>
 static cudaError_t launch_level_w(const LevelArgs& a, uint32_t num_sms, cudaStream_t s, uint32_t* launches) {
-    constexpr int E = 1;  // groups of 128 positions per ranking warp per round
     cudaError_t err;
     {
         ProfScope p("tiles", s);
         tiles_kernel<<<1, 1024, 0, s>>>(a);
     }
-    const size_t csm = classify_smem_bytes(a.k, a.B, W);
-    err = cudaFuncSetAttribute(classify_kernel<W, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+    err = launch_classify(a, W, num_sms, s);
     if (err != cudaSuccess) return err;
-    {
-        ProfScope p("classify", s);
-        classify_kernel<W, E><<<num_sms, kClassifyThreads, csm, s>>>(a);
-    }
     {
         ProfScope p("scan", s);
         scan_kernel<<<num_sms * 2, 512, 0, s>>>(a, a.small_max_m);

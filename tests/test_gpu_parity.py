@@ -187,3 +187,15 @@ def test_parked_chains(park_after):
 ])
 def test_odd_block_sizes(n, w, plan):
     check(n, w, plan, seed=31)
+
+
+# blocks larger than a bucket's shared-memory chunk (a block takes its home slot, or a pool
+# block, when its first chunk is written), and k = 1024 over two levels, the near-capacity plan
+@pytest.mark.parametrize("n,w,plan", [
+    (1 << 22, 4, rip.Plan(ks=[256], Ts=[1 << 19], Bs=[512], base=4096)),
+    (3_000_017, 8, rip.Plan(ks=[128, 64], Ts=[1 << 20, 1 << 20], Bs=[256, 128], base=4096)),
+    (1 << 21, 16, rip.Plan(ks=[64], Ts=[1 << 17], Bs=[256], base=2048)),
+    (1 << 23, 4, rip.Plan(ks=[1024, 1024], Ts=[1 << 21, 1 << 24], Bs=[256, 32], base=4096, max_levels=2)),
+])
+def test_chunked_blocks(n, w, plan):
+    check(n, w, plan, seed=5)
