@@ -88,23 +88,24 @@ namespace {
 
 constexpr uint32_t kMediumGrid = 16;
 constexpr uint32_t kParkAfter = 256;  // chain steps before the permutation parks a block
-constexpr size_t kClassifySmemBudget = 224 * 1024;
 
 struct LevelCaps {
     uint32_t big = 0;       // subproblems that may run in place
-    uint64_t tiles = 0;
+    uint32_t wave = 0;      // of which one wave holds at most this many
+    uint32_t waves = 0;
+    uint64_t tiles = 0;     // per wave
     uint64_t pairs = 0;     // tiles x k
-    uint64_t children = 0;  // big x k
-    uint64_t pool = 0;      // elements
+    uint64_t pool = 0;      // elements, per wave
     uint64_t dem = 0;
 };
 
 struct Layout {
     size_t total = 0;
     size_t arrays, lists_big0, lists_big1, small, medium, bigfy, counts, counters, pool_used;
-    size_t tiles, sp_tile_begin, C, FBc, TLc, tinfo, child, words, pool, dem, parks, mscratch;
-    uint32_t big_cap, small_cap, bigfy_cap, tile_cap, dem_cap, park_cap, levels;
-    uint64_t pair_cap, child_cap, pool_cap, slot_count;
+    size_t tiles, sp_tile_begin, segs, C, FBc, TLc, tinfo, child, words, pool, dem, parks, mscratch;
+    uint32_t big_cap, small_cap, bigfy_cap, tile_cap, dem_cap, park_cap, levels, wave_cap;
+    uint64_t pair_cap, child_cap, pool_cap, slot_cap;
+    uint32_t wave[64], waves[64];  // per level: subproblems per wave, waves
     uint32_t small_max_m;
     uint64_t aux_bytes;
 };
@@ -172,37 +173,47 @@ Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& 
     Layout L{};
     const DevPlan dp = to_dev(p);
     L.small_max_m = small_max_m_for(w);
-    uint64_t nmax = 0, nsum = 0, slots = 0;
-    uint32_t bmin = 0xffffffffu;
-    for (uint32_t l = 0; l < p.num_levels; ++l) bmin = std::min(bmin, p.level[l].block);
+    uint64_t nmax = 0, nsum = 0;
     for (uint64_t n : ns) {
         nmax = std::max(nmax, n);
         nsum += n;
-        slots += align_up((n + bmin - 1) / bmin, 64);  // each array's slot range starts at a multiple of 64
     }
-    L.slot_count = slots;
     const uint32_t narr = (uint32_t)ns.size();
 
-    std::vector<LevelCaps> caps;
-    uint64_t prodk = 1, max_children = 0;
-    uint64_t small_children = narr, bigfy_total = narr;
-    for (uint32_t lev = 0; lev < dp.cap && lev < 64; ++lev) {
-        const uint32_t li = dp.idx(lev);
-        const uint32_t k = p.level[li].k, B = p.level[li].block;
-        const uint64_t T = p.level[li].tile;
-        // smallest subproblem that runs in place at this level
-        uint64_t inplace_min = (uint64_t)kMediumMaxM + 1;
+    // smallest subproblem that runs in place at level lev
+    auto inplace_min_at = [&](uint32_t lev) -> uint64_t {
+        uint64_t im = (uint64_t)kMediumMaxM + 1;
         if (!small_solver_can_scatter(dp, kMediumMaxM, lev)) {  // eligibility is monotone in m
             uint64_t lo = 1, hi = kMediumMaxM;                    // can(lo) or lo == 1, !can(hi)
             while (hi - lo > 1) {
                 const uint64_t mid = (lo + hi) / 2;
                 if (small_solver_can_scatter(dp, mid, lev)) lo = mid; else hi = mid;
             }
-            inplace_min = hi;
+            im = hi;
         }
-        inplace_min = std::max<uint64_t>(inplace_min, dp.base + 1);
-        // per array: expected size at this level; count arrays for which big subproblems are possible
-        uint64_t big = 0, tiles = 0;
+        return std::max<uint64_t>(im, dp.base + 1);
+    };
+    // The slot table holds the segments of one wave.  Level 0 runs every root at once; deeper
+    // levels run their subproblems in waves that fit the same table.
+    uint64_t slot_cap = 64;
+    {
+        const uint64_t B0 = p.level[dp.idx(0)].block, im0 = inplace_min_at(0);
+        uint64_t s0 = 0;
+        for (uint64_t n : ns)
+            if (n >= im0) s0 += align_up((n + B0 - 1) / B0 + 1, 64);
+        slot_cap = std::max<uint64_t>(slot_cap, s0);
+    }
+
+    std::vector<LevelCaps> caps;
+    uint64_t prodk = 1;
+    uint64_t small_children = narr, bigfy_total = narr, max_children = 0;
+    for (uint32_t lev = 0; lev < dp.cap && lev < 64; ++lev) {
+        const uint32_t li = dp.idx(lev);
+        const uint32_t k = p.level[li].k, B = p.level[li].block;
+        const uint64_t T = p.level[li].tile;
+        const uint64_t inplace_min = inplace_min_at(lev);
+        // per array: expected size at this level; count subproblems that may run in place
+        uint64_t big = 0, tiles_all = 0;
         for (uint64_t n : ns) {
             if (n < inplace_min) continue;
             // a subproblem size at level L is Binomial(n, 1/prod k): mean mu, sd <= sqrt(mu)
@@ -210,40 +221,54 @@ Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& 
             if (mu + 10.0 * std::sqrt(mu) + 64.0 < (double)inplace_min) continue;
             const uint64_t cnt = std::min<uint64_t>(prodk, n / inplace_min);
             big += std::max<uint64_t>(cnt, 1);
-            tiles += n / T + std::max<uint64_t>(cnt, 1);
+            tiles_all += n / T + std::max<uint64_t>(cnt, 1);
         }
         if (big == 0) break;
+        const double mu = (double)nmax / (double)prodk;
+        const double m_sub = lev == 0 ? (double)nmax : std::min((double)nmax, mu + 10.0 * std::sqrt(mu) + 64.0);
+        const uint64_t per_sub = align_up((uint64_t)(m_sub / B) + 3, 64);  // slots of one subproblem
         LevelCaps c;
         c.big = (uint32_t)std::min<uint64_t>(big + 16, 0xffffffffull);
-        c.tiles = tiles + 16;
+        if (lev == 0) {
+            c.wave = c.big;
+        } else {
+            slot_cap = std::max(slot_cap, per_sub);
+            const uint64_t wmax = std::max<uint64_t>(1, std::min<uint64_t>(c.big, slot_cap / per_sub));
+            const uint64_t nw = (c.big + wmax - 1) / wmax;
+            c.wave = (uint32_t)((c.big + nw - 1) / nw);  // balanced waves
+        }
+        c.waves = (c.big + c.wave - 1) / c.wave;
+        const uint64_t tiles_per_sub = (uint64_t)std::ceil(m_sub / (double)T);  // m_sub bounds every size
+        c.tiles = std::min<uint64_t>(tiles_all, (uint64_t)c.wave * tiles_per_sub) + 16;
         c.pairs = c.tiles * k;
-        c.children = (uint64_t)c.big * k;
         // tails: (B-1)/2 per (tile, bucket) on average when counts are >> B, with a
         // Hoeffding margin; otherwise every tile-bucket may be a tail
-        const double mu_tile = std::min<double>((double)T, (double)nmax / (double)prodk);
+        const double mu_tile = std::min<double>((double)T, m_sub);
         const double mu_c = mu_tile / k;
         const double pairs = (double)c.pairs;
+        const double wave_elems = std::min((double)nsum, m_sub * c.wave);
         double tails;
         if (mu_c >= 4.0 * B)
             tails = pairs * (B - 1) / 2.0 * 1.05 + 20.0 * B * std::sqrt(pairs) + 4.0 * B * k;
         else
-            tails = std::min<double>(pairs * (B - 1), (double)nsum + B);
+            tails = std::min<double>(pairs * (B - 1), wave_elems + B);
         // demoted blocks: at most one per (subproblem, bucket) plus two per subproblem.
         // With counts >> B the tail total of a bucket is (close to) uniform mod B, so a
         // bucket's last block is demoted with probability <= 1/2: Hoeffding margin.
-        const double dem_worst = std::min<double>((double)c.big * (k + 2), (double)nsum / B + c.big * 2.0);
-        const double pairs_sp = (double)c.big * k;
+        const double dem_worst = std::min<double>((double)c.wave * (k + 2), wave_elems / B + c.wave * 2.0);
+        const double pairs_sp = (double)c.wave * k;
         const double dem_blocks = mu_c >= 4.0 * B
-                                      ? std::min(dem_worst, pairs_sp / 2.0 + 20.0 * std::sqrt(pairs_sp) + 2.0 * c.big)
+                                      ? std::min(dem_worst, pairs_sp / 2.0 + 20.0 * std::sqrt(pairs_sp) + 2.0 * c.wave)
                                       : dem_worst;
         c.dem = (uint64_t)dem_worst + 16;
         c.pool = (uint64_t)(tails + dem_blocks * B) + 64;
         // chunked staging: a block's location is taken at its first chunk, from the pool while
-        // no read home slot is free -- at most k such blocks per tile
+        // no read home slot is free -- at most k (1 - Bs/B) + 1 such blocks per tile
         ClsCfg cc{};
         if (classify_config(k, B, w, &cc) && cc.cpb > 1) {
-            c.pool += c.tiles * k * B;
-            c.dem += c.tiles * k;
+            const uint64_t per_tile = (uint64_t)k * (cc.cpb - 1) / cc.cpb + 1;
+            c.pool += c.tiles * per_tile * B;
+            c.dem += c.tiles * per_tile;
         }
         max_children = std::max<uint64_t>(max_children, (uint64_t)c.big * k);
         caps.push_back(c);
@@ -251,11 +276,16 @@ Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& 
         bigfy_total += (uint64_t)c.big * k;
         prodk = std::min<uint64_t>(prodk * k, (uint64_t)1 << 62);
     }
+    L.slot_cap = slot_cap;
     L.levels = (uint32_t)caps.size();
     uint32_t kmax = 2;
     for (uint32_t l = 0; l < p.num_levels; ++l) kmax = std::max(kmax, p.level[l].k);
-    for (const LevelCaps& c : caps) {
+    for (uint32_t l = 0; l < L.levels; ++l) {
+        const LevelCaps& c = caps[l];
+        L.wave[l] = c.wave;
+        L.waves[l] = c.waves;
         L.big_cap = std::max(L.big_cap, c.big);
+        L.wave_cap = std::max(L.wave_cap, c.wave);
         L.tile_cap = (uint32_t)std::max<uint64_t>(L.tile_cap, c.tiles);
         // each tile's tails and each demoted block are separate 16-byte-rounded allocations
         L.pool_cap = std::max(L.pool_cap, c.pool + (c.tiles + c.dem) * (16 / std::min<uint32_t>(w, 16)));
@@ -265,10 +295,11 @@ Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& 
     L.small_cap = (uint32_t)std::min<uint64_t>(per_level_small + 16, 0x7fffffffull);
     L.bigfy_cap = (uint32_t)std::min<uint64_t>(std::min<uint64_t>(bigfy_total, nsum / 2 + 16) + 16, 0x7fffffffull);
     if (L.big_cap == 0) L.big_cap = 1;
+    if (L.wave_cap == 0) L.wave_cap = 1;
     if (L.tile_cap == 0) L.tile_cap = 1;
     // any level may index (tile, bucket) and (subproblem, bucket) tables with the largest k
     L.pair_cap = (uint64_t)L.tile_cap * kmax;
-    L.child_cap = (uint64_t)L.big_cap * kmax;
+    L.child_cap = (uint64_t)L.wave_cap * kmax;
 
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -287,16 +318,17 @@ Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& 
     L.pool_used = take(sizeof(uint64_t));
     const size_t meta_start = off;
     L.tiles = take(sizeof(TileRef) * L.tile_cap);
-    L.sp_tile_begin = take(sizeof(uint32_t) * L.big_cap);
+    L.sp_tile_begin = take(sizeof(uint32_t) * L.wave_cap);
+    L.segs = take(sizeof(SegDesc) * L.wave_cap);
     L.C = take(sizeof(uint32_t) * L.pair_cap);
     L.FBc = take(sizeof(uint32_t) * L.pair_cap);
     L.TLc = take(sizeof(uint32_t) * L.pair_cap);
     L.tinfo = take(sizeof(TileInfo) * L.tile_cap);
     L.child = take(sizeof(ChildInfo) * L.child_cap);
-    L.words = take(L.levels ? sizeof(uint32_t) * L.slot_count : 0);
+    L.words = take(L.levels ? sizeof(uint32_t) * L.slot_cap : 0);
     L.pool = take(L.levels ? (size_t)w * L.pool_cap : 0);
     L.dem = take(sizeof(DemRec) * L.dem_cap);
-    L.park_cap = L.levels ? (uint32_t)std::min<uint64_t>(65536, slots / 16 + 64) : 0;
+    L.park_cap = L.levels ? (uint32_t)std::min<uint64_t>(65536, L.slot_cap / 16 + 64) : 0;
     L.parks = take(sizeof(ParkRec) * L.park_cap);
     // the medium solver (data in global scratch) runs only for subproblems above the
     // shared-memory limit: children of in-place levels, or a root in that range
@@ -413,15 +445,11 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
     // tuning knob: chain steps before the permutation parks a block (RIP_PARK_AFTER)
     uint32_t park_after = kParkAfter;
     if (const char* env = std::getenv("RIP_PARK_AFTER")) park_after = (uint32_t)std::strtoul(env, nullptr, 10);
-    uint32_t bmin = 0xffffffffu;
-    for (uint32_t l = 0; l < plan.num_levels; ++l) bmin = std::min(bmin, plan.level[l].block);
-    // array table: device pointer, size, seed, slot base
+    // array table: device pointer, size, seed
     std::vector<ArrayDesc> arr(ptrs.size());
-    uint64_t slot = 0;
     bool aligned16 = true;
     for (size_t i = 0; i < ptrs.size(); ++i) {
-        arr[i] = ArrayDesc{ptrs[i], ns[i] > 1 ? ns[i] : 0, base_seed + i, slot};
-        slot += align_up((ns[i] + bmin - 1) / bmin, 64);
+        arr[i] = ArrayDesc{ptrs[i], ns[i] > 1 ? ns[i] : 0, base_seed + i};
         aligned16 &= (reinterpret_cast<uintptr_t>(ptrs[i]) % 16) == 0;
     }
     ArrayDesc* d_arr = reinterpret_cast<ArrayDesc*>(wsp + lay.arrays);
@@ -464,7 +492,7 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
     ia.pool_used = pool_used;
     if (launch_init(ia, stream) != cudaSuccess) return RIP_ECUDA;
     // chain starts scan the whole slot table for words in state 01: start from all zero
-    if (lay.levels && cudaMemsetAsync(wsp + lay.words, 0, sizeof(uint32_t) * lay.slot_count, stream) != cudaSuccess)
+    if (lay.levels && cudaMemsetAsync(wsp + lay.words, 0, sizeof(uint32_t) * lay.slot_cap, stream) != cudaSuccess)
         return RIP_ECUDA;
     ++launches;
 
@@ -519,9 +547,8 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
         a.FBc = reinterpret_cast<uint32_t*>(wsp + lay.FBc);
         a.TLc = reinterpret_cast<uint32_t*>(wsp + lay.TLc);
         a.tinfo = reinterpret_cast<TileInfo*>(wsp + lay.tinfo);
-        a.slot_count = lay.slot_count;
-        a.slot_chunks = (lay.slot_count + 63) / 64;
-        a.narrays = (uint32_t)arr.size();
+        a.slot_cap = lay.slot_cap;
+        a.segs = reinterpret_cast<SegDesc*>(wsp + lay.segs);
         a.child = reinterpret_cast<ChildInfo*>(wsp + lay.child);
         a.words = reinterpret_cast<uint32_t*>(wsp + lay.words);
         a.pool = wsp + lay.pool;
@@ -532,7 +559,12 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
         a.parks = reinterpret_cast<ParkRec*>(wsp + lay.parks);
         a.park_cap = lay.park_cap;
         a.park_after = park_after;
-        if (launch_level(a, w, ds->num_sms, stream, &launches) != cudaSuccess) return RIP_ECUDA;
+        a.wcap = lay.wave[lev];
+        a.wend = lay.wave[lev] * lay.waves[lev];
+        for (uint32_t wv = 0; wv < lay.waves[lev]; ++wv) {  // the level's subproblems, one wave at a time
+            a.wb = wv * lay.wave[lev];
+            if (launch_level(a, w, ds->num_sms, stream, &launches) != cudaSuccess) return RIP_ECUDA;
+        }
         rc = run_small();
         if (rc) return rc;
     }

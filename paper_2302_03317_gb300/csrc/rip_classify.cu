@@ -218,7 +218,8 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
         const uint64_t alo = Sp.o + Sp.eps + lo;  // physical start of the tile's aligned piece
         const uint32_t avail = Sp.m > Sp.eps + lo ? (uint32_t)min((uint64_t)r, Sp.m - Sp.eps - lo) : 0u;
         const uint32_t H = avail / B;
-        const uint64_t hs0 = ad.slot_base + alo / B;
+        const SegDesc seg = a.segs[tr.sp - a.wb];
+        const uint64_t hs0 = seg.base + (alo / B - seg.orig);  // table entry of home slot 0
         const uint64_t P0 = Sp.o + lo;  // logical global position of the tile's first element
         const uint32_t delta = (uint32_t)(P0 & 3u);
         const uint64_t Q0 = P0 >> 2;
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
         // mark them empty so the permutation may fill them.
         if (tr.t == 0 && Sp.eps >= B) {
             const uint64_t first = (Sp.o + B - 1) / B, last = (Sp.o + Sp.eps) / B;
-            for (uint64_t x = first + tid; x < last; x += blockDim.x) a.words[ad.slot_base + x] = 0u;
+            for (uint64_t x = first + tid; x < last; x += blockDim.x) a.words[seg.base + (x - seg.orig)] = 0u;
         }
         for (uint32_t b = tid; b < k; b += blockDim.x) {
             run[b] = 0;

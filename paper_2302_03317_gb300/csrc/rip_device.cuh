@@ -273,7 +273,6 @@ struct ArrayDesc {
     char* data;          // device pointer of the array
     uint64_t n;          // elements
     uint64_t seed;       // Philox key of this array
-    uint64_t slot_base;  // first entry of this array in the slot-word table
 };
 
 // A subproblem: elements [o, o+m) of array `arr` (o is both the logical start

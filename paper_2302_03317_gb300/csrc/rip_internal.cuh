@@ -16,7 +16,8 @@ constexpr uint32_t kPermuteThreads = 256;
 constexpr uint32_t kGroup = 8;            // lanes moving one block in the permutation
 constexpr size_t kSmemOptin = 232448;     // dynamic shared memory per block on sm_100/103
 
-// Slot words (one per B-element slot of the array):
+// Slot words (one per B-element slot of the subproblems of one wave; each subproblem's
+// slots form a segment of the table, starting at a multiple of 64):
 //   bits 31..30 state: 00 empty, 01 holds an unmoved block, 11 claimed, 10 filled
 //   after classification: bits 29..20 bucket, 19..0 block index inside (tile, bucket)
 //   after resolution:     bit 29 "goes to the pool", bits 28..0 destination slot
@@ -26,6 +27,16 @@ constexpr uint32_t kWordTaken = 1u << 31;
 constexpr uint32_t kWordDem = 1u << 29;
 constexpr uint32_t kWordDestMask = (1u << 29) - 1u;
 constexpr uint32_t kBlkBits = 20;
+
+// The slot segment of one subproblem of the current wave: table entries [base, base + nslots)
+// hold grid slots orig .. orig + nslots - 1 of the array (grid slot g = elements [gB, (g+1)B)).
+struct SegDesc {
+    uint64_t base;
+    uint64_t orig;
+    uint64_t nslots;
+    uint32_t arr;
+    uint32_t pad;
+};
 
 struct TileRef {
     uint32_t sp;  // index in the level's big list
@@ -42,7 +53,7 @@ struct TileInfo {
 struct ChildInfo {
     uint64_t o;          // region start (array-relative)
     uint64_t m;          // size
-    uint64_t slot_base;  // slot-table index of full block 0
+    uint64_t slot_base;  // slot-table index of full block 0 (in the parent's segment)
     uint32_t Fb;         // full blocks of the bucket
     uint32_t placed;     // full blocks that go to slots (Fb or Fb-1)
     uint32_t eps;        // rotation of the child region
@@ -111,19 +122,20 @@ struct LevelArgs {
     uint32_t small_max_m;  // largest m whose data fits in shared memory
     // tiles
     TileRef* tiles;
-    uint32_t* sp_tile_begin;  // per big subproblem
-    uint32_t* counters;       // [0] tiles, [1] tile cursor, [2] demoted count, [4..5] chunk cursor, [6] parks
+    uint32_t wb, wcap, wend;  // this wave: big-list entries [wb, wb + wcap); all waves: [0, wend)
+    uint32_t* sp_tile_begin;  // per subproblem of the wave
+    SegDesc* segs;            // per subproblem of the wave
+    uint64_t slot_cap;        // entries of the slot-word table
+    uint32_t* counters;       // [0] tiles, [1] tile cursor, [2] demoted count, [4..5] chunk cursor, [6] parks,
+                              // [7] subproblems of the wave, [8] 64-entry chunks of the wave's segments
     uint64_t* pool_used;
     uint32_t tile_cap;
     uint32_t* C;    // tile_cap x k counts
     uint32_t* FBc;  // tile_cap x k full blocks of earlier tiles
     uint32_t* TLc;  // tile_cap x k tail elements of earlier tiles
     TileInfo* tinfo;
-    ChildInfo* child;       // big_cap x k
+    ChildInfo* child;       // wcap x k, indexed by (subproblem - wb, bucket)
     uint32_t* words;
-    uint64_t slot_count;    // entries of the slot-word table
-    uint64_t slot_chunks;   // 64-entry chunks scanned for chain starts
-    uint32_t narrays;
     char* pool;
     uint64_t pool_cap;    // elements
     uint32_t pool_align;  // elements per 16 bytes: every pool allocation is a multiple of this

@@ -101,43 +101,70 @@ __global__ void init_kernel(InitArgs a) {
 
 __global__ void tiles_kernel(LevelArgs a) {
     __shared__ uint32_t scan[32];
+    __shared__ uint64_t scan64[32];
     __shared__ uint32_t carry;
+    __shared__ uint64_t scarry;
     const uint32_t nbig = min(*a.big_count, a.big_cap);
-    if (threadIdx.x == 0) carry = 0;
+    const uint32_t we = nbig > a.wb ? min(nbig - a.wb, a.wcap) : 0u;  // subproblems of this wave
+    const uint64_t B = a.B;
+    if (threadIdx.x == 0) {
+        carry = 0;
+        scarry = 0;
+    }
     __syncthreads();
-    for (uint32_t c0 = 0; c0 < nbig; c0 += blockDim.x) {
-        const uint32_t sp = c0 + threadIdx.x;
+    for (uint32_t c0 = 0; c0 < we; c0 += blockDim.x) {
+        const uint32_t i = c0 + threadIdx.x;
         uint32_t nt = 0;
-        if (sp < nbig) {
-            const uint64_t m = a.big[sp].m;
-            const uint64_t t64 = a.T >= m ? 1 : (m + a.T - 1) / a.T;
+        uint64_t ns = 0, g0 = 0, ng = 0;
+        uint32_t arr = 0;
+        if (i < we) {
+            const Sub sb = a.big[a.wb + i];
+            const uint64_t t64 = a.T >= sb.m ? 1 : (sb.m + a.T - 1) / a.T;
             nt = (uint32_t)(t64 < 0xffffffffull ? t64 : 0xffffffffull);
+            g0 = sb.o / B;                        // grid slots overlapping [o, o+m)
+            ng = (sb.o + sb.m + B - 1) / B - g0;
+            ns = (ng + 63) & ~63ull;               // segments start at multiples of 64
+            arr = sb.arr;
         }
         uint32_t total;
         const uint32_t ex = block_exclusive_scan<uint32_t>(nt, scan, &total);
+        uint64_t stotal;
+        const uint64_t sex = block_exclusive_scan<uint64_t>(ns, scan64, &stotal);
         const uint32_t begin = carry + ex;
-        if (sp < nbig) {
-            a.sp_tile_begin[sp] = begin;
+        if (i < we) {
+            a.sp_tile_begin[i] = begin;
             for (uint32_t t = 0; t < nt; ++t)
-                if (begin + t < a.tile_cap) a.tiles[begin + t] = TileRef{sp, t};
+                if (begin + t < a.tile_cap) a.tiles[begin + t] = TileRef{a.wb + i, t};
+            a.segs[i] = SegDesc{scarry + sex, g0, ng, arr, 0};
         }
         __syncthreads();
-        if (threadIdx.x == 0) carry += total;
+        if (threadIdx.x == 0) {
+            carry += total;
+            scarry += stotal;
+        }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        if (carry > a.tile_cap) report(a.status, RIP_EWORKSPACE, 0x6101, carry);
-        a.counters[0] = min(carry, a.tile_cap);
-        a.counters[1] = 0;
-        a.counters[2] = 0;
-        a.counters[3] = 0;
-        a.counters[4] = 0;
-        a.counters[5] = 0;
-        a.counters[6] = 0;
+        bool ok = true;
+        if (carry > a.tile_cap) {
+            report(a.status, RIP_EWORKSPACE, 0x6101, carry);
+            ok = false;
+        }
+        if (scarry > a.slot_cap) {  // the wave's segments do not fit the table: skip the wave
+            report(a.status, RIP_EWORKSPACE, 0x6103, scarry);
+            ok = false;
+        }
+        a.counters[0] = ok ? carry : 0u;
+        for (int c = 1; c <= 6; ++c) a.counters[c] = 0;
+        a.counters[7] = ok ? we : 0u;
+        a.counters[8] = ok ? (uint32_t)(scarry / 64u) : 0u;
         *a.pool_used = 0;
-        *a.next_big_count = 0;
-        *a.small_count = 0;
-        *a.medium_count = 0;
+        if (a.wb == 0 && nbig > a.wend) report(a.status, RIP_EWORKSPACE, 0x6104, nbig);  // more than planned
+        if (a.wb == 0) {  // the next level's lists fill over all waves of this one
+            *a.next_big_count = 0;
+            *a.small_count = 0;
+            *a.medium_count = 0;
+        }
     }
 }
 
@@ -147,12 +174,13 @@ __global__ void scan_kernel(LevelArgs a, uint32_t small_max_m) {
     __shared__ uint64_t start[kMaxK];
     __shared__ uint64_t scan64[32];
     const uint32_t k = a.k, B = a.B;
-    const uint32_t nbig = min(*a.big_count, a.big_cap);
-    for (uint32_t sp = blockIdx.x; sp < nbig; sp += gridDim.x) {
+    const uint32_t we = a.counters[7];
+    for (uint32_t wi = blockIdx.x; wi < we; wi += gridDim.x) {
+        const uint32_t sp = a.wb + wi;
         const Sub S = a.big[sp];
-        const ArrayDesc ad = a.arrays[S.arr];
+        const SegDesc seg = a.segs[wi];
         const uint32_t nt = (uint32_t)(a.T >= S.m ? 1 : (S.m + a.T - 1) / a.T);
-        const uint32_t tb = a.sp_tile_begin[sp];
+        const uint32_t tb = a.sp_tile_begin[wi];
         if ((uint64_t)tb + nt > a.counters[0]) {  // tile list overflowed (reported by tiles_kernel)
             if (threadIdx.x == 0) report(a.status, RIP_EWORKSPACE, 0x6102, tb);
             continue;
@@ -173,7 +201,7 @@ __global__ void scan_kernel(LevelArgs a, uint32_t small_max_m) {
             ChildInfo ci{};
             ci.Fb = fsum;
             ci.placed = rsum;  // tails, temporarily
-            a.child[(uint64_t)sp * k + b] = ci;
+            a.child[(uint64_t)wi * k + b] = ci;
         }
         __syncthreads();
         {
@@ -185,7 +213,7 @@ __global__ void scan_kernel(LevelArgs a, uint32_t small_max_m) {
         }
         __syncthreads();
         for (uint32_t b = threadIdx.x; b < k; b += blockDim.x) {
-            ChildInfo ci = a.child[(uint64_t)sp * k + b];
+            ChildInfo ci = a.child[(uint64_t)wi * k + b];
             const uint32_t tails = ci.placed;
             const uint64_t sb = start[b];
             const uint64_t se = b + 1 < k ? start[b + 1] : S.m;
@@ -194,8 +222,8 @@ __global__ void scan_kernel(LevelArgs a, uint32_t small_max_m) {
             const uint32_t e0 = (uint32_t)((B - ci.o % B) % B);
             ci.eps = ci.m > e0 ? e0 : 0;
             ci.placed = ci.Fb >= 1 ? (e0 <= tails ? ci.Fb : ci.Fb - 1) : 0;
-            ci.slot_base = ad.slot_base + (ci.o + e0) / B;
-            a.child[(uint64_t)sp * k + b] = ci;
+            ci.slot_base = seg.base + ((ci.o + e0) / B - seg.orig);
+            a.child[(uint64_t)wi * k + b] = ci;
             const Sub c{ci.o, ci.m, S.arr, S.level + 1, ci.eps, 0};
             route_sub(c, a.plan, small_max_m, a.next_big, a.next_big_count, a.big_cap, a.small, a.small_count,
                       a.medium, a.medium_count, a.small_cap, a.bigfy, a.bigfy_count, a.bigfy_cap, a.status);
@@ -217,7 +245,7 @@ __global__ void resolve_kernel(LevelArgs a) {
             if ((w & (kWordOcc | kWordTaken)) != kWordOcc) continue;  // empty: held a part of a tail only
             const uint32_t b = (w >> kBlkBits) & (kMaxK - 1u);
             const uint32_t blk = w & ((1u << kBlkBits) - 1u);
-            const ChildInfo ci = a.child[(uint64_t)tr.sp * k + b];
+            const ChildInfo ci = a.child[(uint64_t)(tr.sp - a.wb) * k + b];
             const uint32_t J = a.FBc[(uint64_t)tile * k + b] + blk;
             uint32_t nw;
             if (J < ci.placed) {
@@ -269,24 +297,27 @@ __global__ void __launch_bounds__(kPermuteThreads) permute_kernel(LevelArgs a, u
                 uint64_t c0 = 0;
                 if (leader) c0 = atomicAdd((unsigned long long*)&a.counters[4], 1ull);
                 chunk = __shfl_sync(gmask, c0, leader_lane);
-                if (chunk >= a.slot_chunks) break;
+                if (chunk >= a.counters[8]) break;
                 const uint64_t s0 = chunk * 64u + lg * 8u;
 #pragma unroll
-                for (uint32_t j = 0; j < 8; ++j) cw[j] = s0 + j < a.slot_count ? ld_relaxed(&a.words[s0 + j]) : 0u;
+                for (uint32_t j = 0; j < 8; ++j) cw[j] = ld_relaxed(&a.words[s0 + j]);
                 cpos = 0;
-                // the array holding this chunk (array slot ranges start at multiples of 64)
-                uint32_t lo = 0, hi = a.narrays;
+                // the segment holding this chunk (segments start at multiples of 64)
+                uint32_t lo = 0, hi = a.counters[7];
                 if (leader) {
                     while (hi - lo > 1) {
                         const uint32_t mid = (lo + hi) >> 1;
-                        if (a.arrays[mid].slot_base <= chunk * 64u) lo = mid; else hi = mid;
+                        if (a.segs[mid].base <= chunk * 64u) lo = mid; else hi = mid;
                     }
                 }
                 lo = __shfl_sync(gmask, lo, leader_lane);
-                const ArrayDesc ad = a.arrays[lo];
-                abase = ad.data;
-                aslot = ad.slot_base;
-                anslots = ad.n / a.B;  // whole slots of the array
+                const SegDesc sg = a.segs[lo];
+                const ArrayDesc ad = a.arrays[sg.arr];
+                aslot = sg.base;
+                // whole grid slots of the array inside the segment
+                const uint64_t whole = ad.n / a.B > sg.orig ? ad.n / a.B - sg.orig : 0;
+                anslots = sg.nslots < whole ? sg.nslots : whole;
+                abase = ad.data + sg.orig * slot_bytes;
             }
             // next candidate holding an unmoved block
             const uint32_t owner = cpos >> 3;
@@ -458,7 +489,7 @@ __global__ void tails_kernel(LevelArgs a) {
             const uint64_t ci_idx = (uint64_t)tile * k + b;
             const uint32_t R = a.C[ci_idx] % B;
             if (R == 0) continue;
-            const ChildInfo ci = a.child[(uint64_t)tr.sp * k + b];
+            const ChildInfo ci = a.child[(uint64_t)(tr.sp - a.wb) * k + b];
             const uint64_t x0 = (uint64_t)B * ci.Fb + a.TLc[ci_idx];
             const T* src = pool + ti.pool_base + pre[b];
             const uint64_t n_arr = a.arrays[S.arr].n;
@@ -504,7 +535,7 @@ __global__ void demoted_kernel(LevelArgs a) {
     const T* pool = reinterpret_cast<const T*>(a.pool);
     for (uint32_t i = gw; i < ndem; i += nw) {
         const DemRec rec = a.dem[i];
-        const ChildInfo ci = a.child[(uint64_t)rec.sp * a.k + rec.b];
+        const ChildInfo ci = a.child[(uint64_t)(rec.sp - a.wb) * a.k + rec.b];
         const uint64_t J = (uint64_t)a.FBc[(uint64_t)rec.tile * a.k + rec.b] + rec.blk;
         const ArrayDesc ad = a.arrays[a.big[rec.sp].arr];
         T* base = reinterpret_cast<T*>(ad.data);
