@@ -89,6 +89,16 @@ typedef struct {
  * per subproblem.  Returns RIP_EINVAL for a NULL plan or bad elem_bytes. */
 int rip_default_plan(uint64_t n, uint32_t elem_bytes, rip_plan *plan);
 
+/* Fills *plan with a plan for inputs that fill most of the device (the
+ * in-place requirement of Sec. 3 at its largest): k = 1024 buckets over two
+ * levels, then Fisher-Yates (max_levels 2, base 4096); root blocks of 1 KiB and
+ * root tiles one per streaming multiprocessor; 32-element blocks and one tile
+ * per subproblem at level 1.  For 2^34 elements its workspace is 0.86% of a
+ * 4-byte input and 0.63% of an 8-byte one; the root level's fixed part (tails
+ * and blocks of 152 tiles x 1024 buckets) makes the fraction larger for
+ * smaller inputs.  Returns RIP_EINVAL for a NULL plan or bad elem_bytes. */
+int rip_capacity_plan(uint64_t n, uint32_t elem_bytes, rip_plan *plan);
+
 /* Bytes of device workspace rip_shuffle_ex needs for (n, elem_bytes, plan);
  * plan NULL = default plan.  Returns 0 if the arguments are invalid. */
 size_t rip_shuffle_workspace_size(uint64_t n, uint32_t elem_bytes, const rip_plan *plan);

@@ -73,6 +73,13 @@ def _load():
         lib.oracle_shuffle_many.restype = i32
         lib.oracle_hash.argtypes = [vp, u64, u32]
         lib.oracle_hash.restype = u64
+        lib.oracle_hash_at.argtypes = [vp, u64, u32, u64]
+        lib.oracle_hash_at.restype = u64
+        lib.oracle_level_counts.argtypes = [u64, u64, u64, u32, u32, u64, u64, u64, vp]
+        lib.oracle_level_counts.restype = i32
+        lib.oracle_level_place_iota.argtypes = [u64, u32, u64, u64, u32, u32, u64, u32, u64, u64, u32, u32,
+                                                vp, vp, vp, vp, vp, vp, u64, u64]
+        lib.oracle_level_place_iota.restype = i32
         _lib = lib
         return lib
 
@@ -236,3 +243,82 @@ def digest(a: np.ndarray) -> int:
     """Position-dependent 64-bit digest (splitmix64-based), see rip_oracle.c."""
     a = np.ascontiguousarray(a)
     return int(_load().oracle_hash(a.ctypes.data, a.shape[0], _elem_bytes(a)))
+
+
+def _pieces(lo: int, hi: int, parts: int):
+    step = max(1, -(-(hi - lo) // max(1, parts)))
+    return [(a, min(a + step, hi)) for a in range(lo, hi, step)]
+
+
+def iota_digest_and_ranges(n: int, w: int, seed: int, plan: Plan, ranges, threads: int = 0,
+                           budget_bytes: int = 8 << 30):
+    """Digest and sampled ranges of shuffle(iota(n)), for n too large to hold twice.
+
+    The root level is evaluated piecewise from its definition (oracle_level_counts,
+    oracle_level_place_iota: the layout of oracle_scatter_level), a group of root buckets
+    at a time; every root bucket is then finished by shuffle_sub (level 1 onward).  The
+    digest is the sum of the pieces' digests (oracle_hash_at); ``ranges`` is a list of
+    (start, length) whose output elements are returned.  iota: element p has value p
+    (u32: p mod 2^32).  Threads run independent pieces only.
+    """
+    from concurrent.futures import ThreadPoolExecutor
+    if w not in (4, 8):
+        raise ValueError("iota inputs are 4- or 8-byte elements")
+    dt = np.uint32 if w == 4 else np.uint64
+    cap = plan.max_levels if plan.max_levels else 64
+    if n <= plan.base or cap == 0:
+        raise ValueError("the root is a leaf: use shuffle() directly")
+    lib = _load()
+    k, T, B = int(plan.ks[0]), int(plan.Ts[0]), int(plan.Bs[0])
+    tiles = -(-n // T)
+    threads = threads or os.cpu_count() or 1
+    cnt = np.zeros((tiles, k), dtype=np.uint64)
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        futs = [ex.submit(lib.oracle_level_counts, n, seed, 0, 0, k, T, a, b, cnt[a:b].ctypes.data)
+                for a, b in _pieces(0, tiles, 4 * threads)]
+        for f in futs:
+            if f.result():
+                raise RuntimeError("oracle_level_counts failed")
+    sizes = cnt.sum(axis=0)
+    full = cnt // np.uint64(B)
+    tail = cnt % np.uint64(B)
+    full_before = np.ascontiguousarray(np.cumsum(full, axis=0, dtype=np.uint64) - full)
+    tail_before = np.ascontiguousarray(np.cumsum(tail, axis=0, dtype=np.uint64) - tail)
+    full_total = np.ascontiguousarray(full.sum(axis=0, dtype=np.uint64))
+    start = np.zeros(k + 1, dtype=np.uint64)
+    start[1:] = np.cumsum(sizes, dtype=np.uint64)
+    got = [np.empty(length, dtype=dt) for _, length in ranges]
+    h = 0
+    b0 = 0
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        while b0 < k:
+            b1 = b0 + 1
+            while b1 < k and int(start[b1 + 1] - start[b0]) * w <= budget_bytes:
+                b1 += 1
+            base, length = int(start[b0]), int(start[b1] - start[b0])
+            region = np.empty(length, dtype=dt)
+            futs = [ex.submit(lib.oracle_level_place_iota, n, w, seed, 0, 0, k, T, B, a, b, b0, b1,
+                              cnt.ctypes.data, full_before.ctypes.data, tail_before.ctypes.data,
+                              start.ctypes.data, full_total.ctypes.data, region.ctypes.data, base, length)
+                    for a, b in _pieces(0, tiles, 4 * threads)]
+            for f in futs:
+                if f.result():
+                    raise RuntimeError("oracle_level_place_iota failed")
+            futs = []
+            for b in range(b0, b1):
+                s0, s1 = int(start[b]) - base, int(start[b + 1]) - base
+                if s1 - s0 > 1:
+                    futs.append(ex.submit(shuffle_sub, region[s0:s1], seed, int(start[b]), 1, plan))
+            for f in futs:
+                f.result()
+            parts = _pieces(0, length, 4 * threads)
+            futs = [ex.submit(lib.oracle_hash_at, region[a:b].ctypes.data, b - a, w, base + a) for a, b in parts]
+            for f in futs:
+                h = (h + int(f.result())) & 0xFFFFFFFFFFFFFFFF
+            for (r0, rl), dst in zip(ranges, got):
+                lo, hi = max(r0, base), min(r0 + rl, base + length)
+                if lo < hi:
+                    dst[lo - r0:hi - r0] = region[lo - base:hi - base]
+            del region
+            b0 = b1
+    return h, got

@@ -358,6 +358,27 @@ static uint64_t splitmix64(uint64_t x)
  *   H = sum_p splitmix64(p * 0x9E3779B97F4A7C15 ^ v(p))  (mod 2^64),
  *   v = chain of splitmix64 over the element's 8-byte little-endian words
  *   (a short last word is zero-padded). */
+/* Digest of n elements that sit at positions p0 .. p0+n-1 of a longer array:
+ * the position-dependent sum above restricted to those positions (the digest
+ * of a whole array is the sum of the digests of its pieces, mod 2^64). */
+uint64_t oracle_hash_at(const void *data, uint64_t n, uint32_t w, uint64_t p0)
+{
+    const unsigned char *x = (const unsigned char *)data;
+    uint64_t h = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        uint64_t p = p0 + i;
+        uint64_t v = 0;
+        for (uint32_t off = 0; off < w; off += 8) {
+            uint64_t word = 0;
+            uint32_t len = (w - off) < 8 ? (w - off) : 8;
+            for (uint32_t c = 0; c < len; ++c) word |= (uint64_t)x[i * w + off + c] << (8 * c);
+            v = splitmix64(v ^ word);
+        }
+        h += splitmix64(p * 0x9E3779B97F4A7C15ull ^ v);
+    }
+    return h;
+}
+
 uint64_t oracle_hash(const void *data, uint64_t n, uint32_t w)
 {
     const unsigned char *x = (const unsigned char *)data;
@@ -387,5 +408,96 @@ int oracle_shuffle_many(const void *tmpl, uint64_t n, uint32_t w, uint64_t seed0
         int rc = oracle_shuffle(dst + r * n * w, n, w, seed0 + r, num_levels, ks, Ts, Bs, base, max_levels);
         if (rc) return rc;
     }
+    return 0;
+}
+
+/* ---------------------------------------------------------------- streaming level */
+
+/* The canonical layout of one scatter level (oracle_scatter_level) for an
+ * input too large to hold twice, when element values are a function of their
+ * position ("iota": the element at array position p has value p, truncated to
+ * w bytes for w < 8, and p in its first 8 bytes otherwise).  The same
+ * definitions, evaluated piecewise: counts for a range of tiles, then the
+ * placement of the elements of a range of tiles whose buckets lie in a range
+ * of buckets.  Used to check near-capacity runs by digest and sampled ranges
+ * (the subproblems the level creates are then finished by oracle_shuffle_sub).
+ * Four consecutive positions share one Philox call exactly as oracle_bucket
+ * defines (word pos & 3 of the call for pos >> 2). */
+
+static void quad_buckets(uint64_t seed, uint32_t level, uint64_t o, uint64_t q, uint32_t k, uint32_t b[4])
+{
+    uint32_t out[4];
+    philox_seeded(seed, (uint32_t)q, (uint32_t)(q >> 32), level | (TAG_SCATTER << 8), (uint32_t)o, out);
+    for (int j = 0; j < 4; ++j) b[j] = (uint32_t)(((uint64_t)out[j] * (uint64_t)k) >> 32);
+}
+
+/* cnt[(t - t_lo) * k + b] = number of elements of tile t in bucket b, t in [t_lo, t_hi);
+ * the subproblem holds positions o .. o+m-1. */
+int oracle_level_counts(uint64_t m, uint64_t seed, uint64_t o, uint32_t level, uint32_t k, uint64_t T,
+                        uint64_t t_lo, uint64_t t_hi, uint64_t *cnt)
+{
+    if (T == 0 || k == 0) return -1;
+    memset(cnt, 0, (t_hi - t_lo) * k * sizeof(uint64_t));
+    for (uint64_t t = t_lo; t < t_hi; ++t) {
+        uint64_t lo = t * T, hi = lo + T < m ? lo + T : m;
+        uint64_t *c = cnt + (t - t_lo) * k;
+        uint64_t i = lo;
+        while (i < hi) {
+            uint64_t pos = o + i;
+            uint32_t b[4];
+            quad_buckets(seed, level, o, pos >> 2, k, b);
+            for (uint64_t j = pos & 3; j < 4 && i < hi; ++j, ++i) c[b[j]] += 1;
+        }
+    }
+    return 0;
+}
+
+static void iota_value(uint64_t p, uint32_t w, unsigned char *dst)
+{
+    memset(dst, 0, w);
+    for (uint32_t c = 0; c < 8 && c < w; ++c) dst[c] = (unsigned char)(p >> (8 * c));
+}
+
+/* Places the elements of tiles [t_lo, t_hi) whose bucket is in [b_lo, b_hi) at
+ * their level output positions (relative to o), writing those in
+ * [out_base, out_base + out_len) to out.  cnt, full_before and tail_before are
+ * indexed by (tile, bucket) over all tiles of the subproblem; start and
+ * full_total by bucket -- all as oracle_scatter_level defines them. */
+int oracle_level_place_iota(uint64_t m, uint32_t w, uint64_t seed, uint64_t o, uint32_t level, uint32_t k,
+                            uint64_t T, uint32_t B, uint64_t t_lo, uint64_t t_hi, uint32_t b_lo, uint32_t b_hi,
+                            const uint64_t *cnt, const uint64_t *full_before, const uint64_t *tail_before,
+                            const uint64_t *start, const uint64_t *full_total, void *out, uint64_t out_base,
+                            uint64_t out_len)
+{
+    unsigned char *dst = (unsigned char *)out;
+    uint64_t *rank = (uint64_t *)calloc((uint64_t)k + 1, sizeof(uint64_t));
+    if (!rank || T == 0 || B == 0) {
+        free(rank);
+        return -1;
+    }
+    for (uint64_t t = t_lo; t < t_hi; ++t) {
+        memset(rank, 0, (uint64_t)k * sizeof(uint64_t));
+        uint64_t lo = t * T, hi = lo + T < m ? lo + T : m;
+        uint64_t i = lo;
+        while (i < hi) {
+            uint64_t pos = o + i;
+            uint32_t bq[4];
+            quad_buckets(seed, level, o, pos >> 2, k, bq);
+            for (uint64_t j = pos & 3; j < 4 && i < hi; ++j, ++i) {
+                uint32_t b = bq[j];
+                uint64_t r = rank[b]++;
+                if (b < b_lo || b >= b_hi) continue;
+                uint64_t idx = t * k + b;
+                uint64_t in_full = (cnt[idx] / B) * B;
+                uint64_t dest;
+                if (r < in_full)
+                    dest = start[b] + full_before[idx] * B + r;
+                else
+                    dest = start[b] + full_total[b] * B + tail_before[idx] + (r - in_full);
+                if (dest >= out_base && dest - out_base < out_len) iota_value(o + i, w, dst + (dest - out_base) * w);
+            }
+        }
+    }
+    free(rank);
     return 0;
 }

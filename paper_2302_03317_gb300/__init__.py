@@ -90,6 +90,8 @@ def _load():
         pplan = ctypes.POINTER(rip_plan)
         lib.rip_default_plan.argtypes = [u64, u32, pplan]
         lib.rip_default_plan.restype = i32
+        lib.rip_capacity_plan.argtypes = [u64, u32, pplan]
+        lib.rip_capacity_plan.restype = i32
         lib.rip_shuffle_workspace_size.argtypes = [u64, u32, pplan]
         lib.rip_shuffle_workspace_size.restype = sz
         lib.rip_shuffle.argtypes = [vp, u64, u32, u64, vp]
@@ -140,6 +142,12 @@ def _plan_ptr(plan):
 def rip_default_plan(n: int, elem_bytes: int) -> Plan:
     p = rip_plan()
     _check(_load().rip_default_plan(n, elem_bytes, ctypes.byref(p)), "rip_default_plan")
+    return Plan.from_c(p)
+
+
+def rip_capacity_plan(n: int, elem_bytes: int) -> Plan:
+    p = rip_plan()
+    _check(_load().rip_capacity_plan(n, elem_bytes, ctypes.byref(p)), "rip_capacity_plan")
     return Plan.from_c(p)
 
 

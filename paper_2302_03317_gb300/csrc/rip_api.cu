@@ -86,7 +86,7 @@ void prof_end(cudaStream_t s) {
 
 namespace {
 
-constexpr uint32_t kMediumGrid = 16;
+constexpr uint32_t kMediumGrid = 16;  // CTAs of the medium solver when medium subproblems are expected
 constexpr uint32_t kParkAfter = 256;  // chain steps before the permutation parks a block
 
 struct LevelCaps {
@@ -103,7 +103,8 @@ struct Layout {
     size_t total = 0;
     size_t arrays, lists_big0, lists_big1, small, medium, bigfy, counts, counters, pool_used;
     size_t tiles, sp_tile_begin, segs, C, FBc, TLc, tinfo, child, words, pool, dem, parks, mscratch;
-    uint32_t big_cap, small_cap, bigfy_cap, tile_cap, dem_cap, park_cap, levels, wave_cap;
+    uint32_t big_cap, small_cap, medium_cap, bigfy_cap, tile_cap, dem_cap, park_cap, levels, wave_cap;
+    uint32_t medium_grid;
     uint64_t pair_cap, child_cap, pool_cap, slot_cap;
     uint32_t wave[64], waves[64];  // per level: subproblems per wave, waves
     uint32_t small_max_m;
@@ -204,6 +205,20 @@ Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& 
         slot_cap = std::max<uint64_t>(slot_cap, s0);
     }
 
+    // Subproblems above the shared-memory limit (medium solver) or the on-SM limit (large
+    // leaves) are rare: a child size is Binomial(m, 1/k), whose upper tail beyond t = mu + d
+    // is at most exp(-d^2 / (2 (mu + d/3))) (Bernstein).  Their lists are sized by the
+    // expected count with a wide margin, never beyond the count that fits the input.
+    auto tail = [](double mu, double t) {
+        if (t <= mu) return 1.0;
+        const double d = t - mu;
+        return std::exp(-d * d / (2.0 * (mu + d / 3.0)));
+    };
+    double e_med = 0, e_big = 0;
+    for (uint64_t n : ns) {
+        if (n > L.small_max_m && n <= kMediumMaxM) e_med += 1;
+        if (n > kMediumMaxM) e_big += 1;
+    }
     std::vector<LevelCaps> caps;
     uint64_t prodk = 1;
     uint64_t small_children = narr, bigfy_total = narr, max_children = 0;
@@ -271,6 +286,9 @@ Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& 
             c.dem += c.tiles * per_tile;
         }
         max_children = std::max<uint64_t>(max_children, (uint64_t)c.big * k);
+        const double mu_child = (double)nmax / ((double)prodk * k);
+        e_med += (double)c.big * k * tail(mu_child, (double)L.small_max_m);
+        e_big += (double)c.big * k * tail(mu_child, (double)kMediumMaxM);
         caps.push_back(c);
         small_children += (uint64_t)c.big * k;
         bigfy_total += (uint64_t)c.big * k;
@@ -293,7 +311,11 @@ Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& 
     }
     const uint64_t per_level_small = std::max<uint64_t>(narr, max_children);
     L.small_cap = (uint32_t)std::min<uint64_t>(per_level_small + 16, 0x7fffffffull);
-    L.bigfy_cap = (uint32_t)std::min<uint64_t>(std::min<uint64_t>(bigfy_total, nsum / 2 + 16) + 16, 0x7fffffffull);
+    const double det_med = (double)nsum / (L.small_max_m + 1.0) + narr + 16.0;
+    const double det_big = (double)nsum / (kMediumMaxM + 1.0) + narr + 16.0;
+    L.medium_cap = (uint32_t)std::min<double>({det_med, e_med + 10.0 * std::sqrt(e_med) + 64.0, (double)L.small_cap});
+    L.bigfy_cap = (uint32_t)std::min<double>({det_big, e_big + 10.0 * std::sqrt(e_big) + 64.0, (double)bigfy_total + 16.0});
+    L.medium_grid = e_med < 4.0 ? 2u : kMediumGrid;
     if (L.big_cap == 0) L.big_cap = 1;
     if (L.wave_cap == 0) L.wave_cap = 1;
     if (L.tile_cap == 0) L.tile_cap = 1;
@@ -311,7 +333,7 @@ Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& 
     L.lists_big0 = take(sizeof(Sub) * L.big_cap);
     L.lists_big1 = take(sizeof(Sub) * L.big_cap);
     L.small = take(sizeof(Sub) * L.small_cap);
-    L.medium = take(sizeof(Sub) * L.small_cap);
+    L.medium = take(sizeof(Sub) * L.medium_cap);
     L.bigfy = take(sizeof(Sub) * L.bigfy_cap);
     L.counts = take(sizeof(uint32_t) * 8);
     L.counters = take(sizeof(uint32_t) * 16);
@@ -334,7 +356,7 @@ Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& 
     // shared-memory limit: children of in-place levels, or a root in that range
     bool need_medium = L.levels > 0;
     for (uint64_t n : ns) need_medium |= n > L.small_max_m && n <= kMediumMaxM;
-    L.mscratch = take(need_medium ? (size_t)kMediumGrid * kMediumMaxM * w : 0);
+    L.mscratch = take(need_medium ? (size_t)L.medium_grid * kMediumMaxM * w : 0);
     L.total = off;
     (void)meta_start;
     L.aux_bytes = off;
@@ -363,6 +385,31 @@ bool default_plan_impl(uint64_t n, uint32_t w, rip_plan* p, uint32_t num_sms) {
     p->level[1].tile = std::min<uint64_t>((uint64_t)B << 20, (uint64_t)1 << 40) / B * B;
     p->base = 4096;
     p->max_levels = 0;
+    return true;
+}
+
+// Plan for inputs that fill most of the device (the near-capacity case): k = 1024 buckets
+// over two levels, then Fisher-Yates; blocks of 1 KiB at the root (the slot table costs 4
+// bytes per block) and 32 elements below (the tails of the 2^20 deeper tiles cost about
+// B/2 elements each); root tiles one per SM, one tile per level-1 subproblem.
+bool capacity_plan_impl(uint64_t n, uint32_t w, rip_plan* p, uint32_t num_sms) {
+    if (!valid_w(w) || !p) return false;
+    std::memset(p, 0, sizeof(*p));
+    const uint32_t k = 1024;
+    const uint32_t B0 = 1024u / w, B1 = 32;
+    uint64_t T0 = (n + num_sms - 1) / std::max<uint32_t>(num_sms, 1);
+    T0 = std::max<uint64_t>(T0, (uint64_t)B0 * 64);
+    T0 = (T0 + B0 - 1) / B0 * B0;
+    T0 = std::min<uint64_t>(T0, (uint64_t)B0 << 20) / B0 * B0;
+    p->num_levels = 2;
+    p->level[0].k = k;
+    p->level[0].block = B0;
+    p->level[0].tile = T0;
+    p->level[1].k = k;
+    p->level[1].block = B1;
+    p->level[1].tile = (uint64_t)B1 << 20;
+    p->base = 4096;
+    p->max_levels = 2;
     return true;
 }
 
@@ -474,6 +521,7 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
     lists.medium = reinterpret_cast<Sub*>(wsp + lay.medium);
     lists.medium_count = counts + 3;
     lists.small_cap = lay.small_cap;
+    lists.medium_cap = lay.medium_cap;
     lists.bigfy = reinterpret_cast<Sub*>(wsp + lay.bigfy);
     lists.bigfy_count = counts + 4;
     lists.bigfy_cap = lay.bigfy_cap;
@@ -500,10 +548,10 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
         SmallArgs sa{lists.small, lists.small_count, lists.small_cap, d_arr, dplan, ds->status, nullptr, 0, 0};
         const size_t smem = small_smem_bytes(lay.small_max_m, w, false);
         if (launch_small(sa, w, smem, ds->num_sms, stream) != cudaSuccess) return RIP_ECUDA;
-        SmallArgs ma{lists.medium, lists.medium_count, lists.small_cap, d_arr, dplan, ds->status,
+        SmallArgs ma{lists.medium, lists.medium_count, lists.medium_cap, d_arr, dplan, ds->status,
                      wsp + lay.mscratch, (uint64_t)kMediumMaxM * w, 1};
         const size_t msmem = small_smem_bytes(kMediumMaxM, w, true);
-        if (launch_small(ma, w, msmem, kMediumGrid, stream) != cudaSuccess) return RIP_ECUDA;
+        if (launch_small(ma, w, msmem, lay.medium_grid, stream) != cudaSuccess) return RIP_ECUDA;
         launches += 2;
         return RIP_OK;
     };
@@ -534,6 +582,7 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
         a.medium = lists.medium;
         a.medium_count = lists.medium_count;
         a.small_cap = lay.small_cap;
+        a.medium_cap = lay.medium_cap;
         a.bigfy = lists.bigfy;
         a.bigfy_count = lists.bigfy_count;
         a.bigfy_cap = lay.bigfy_cap;
@@ -588,6 +637,12 @@ int rip_default_plan(uint64_t n, uint32_t elem_bytes, rip_plan* plan) {
     if (!plan || !valid_w(elem_bytes)) return RIP_EINVAL;
     DevState* ds = dev_state(nullptr);
     return default_plan_impl(n, elem_bytes, plan, ds ? ds->num_sms : 152) ? RIP_OK : RIP_EINVAL;
+}
+
+int rip_capacity_plan(uint64_t n, uint32_t elem_bytes, rip_plan* plan) {
+    if (!plan || !valid_w(elem_bytes)) return RIP_EINVAL;
+    DevState* ds = dev_state(nullptr);
+    return capacity_plan_impl(n, elem_bytes, plan, ds ? ds->num_sms : 152) ? RIP_OK : RIP_EINVAL;
 }
 
 size_t rip_shuffle_workspace_size(uint64_t n, uint32_t elem_bytes, const rip_plan* plan) {

@@ -79,7 +79,7 @@ struct Lists {
     uint32_t* small_count;
     Sub* medium;
     uint32_t* medium_count;
-    uint32_t small_cap;
+    uint32_t small_cap, medium_cap;
     Sub* bigfy;
     uint32_t* bigfy_count;
     uint32_t bigfy_cap;
@@ -115,7 +115,7 @@ struct LevelArgs {
     uint32_t* small_count;
     Sub* medium;
     uint32_t* medium_count;
-    uint32_t small_cap;
+    uint32_t small_cap, medium_cap;
     Sub* bigfy;
     uint32_t* bigfy_count;
     uint32_t bigfy_cap;

@@ -58,7 +58,7 @@ __device__ __forceinline__ bool push_sub(Sub* list, uint32_t* count, uint32_t ca
 // Route a subproblem to the list that will process it.
 __device__ void route_sub(const Sub& c, const DevPlan& plan, uint32_t small_max_m, Sub* next_big,
                           uint32_t* next_big_count, uint32_t big_cap, Sub* small, uint32_t* small_count,
-                          Sub* medium, uint32_t* medium_count, uint32_t small_cap, Sub* bigfy,
+                          Sub* medium, uint32_t* medium_count, uint32_t small_cap, uint32_t medium_cap, Sub* bigfy,
                           uint32_t* bigfy_count, uint32_t bigfy_cap, Status* st) {
     if (c.m <= 1) return;
     const bool leaf = plan.is_leaf(c.m, c.level);
@@ -66,7 +66,7 @@ __device__ void route_sub(const Sub& c, const DevPlan& plan, uint32_t small_max_
     if (c.m <= small_max_m && solver_ok)
         push_sub(small, small_count, small_cap, c, st, 0x6001);
     else if (c.m <= kMediumMaxM && solver_ok)
-        push_sub(medium, medium_count, small_cap, c, st, 0x6002);
+        push_sub(medium, medium_count, medium_cap, c, st, 0x6002);
     else if (leaf)
         push_sub(bigfy, bigfy_count, bigfy_cap, c, st, 0x6003);
     else
@@ -92,7 +92,7 @@ __global__ void init_kernel(InitArgs a) {
         const ArrayDesc ad = a.arrays[i];
         Sub s{0, ad.n, i, 0, 0, 0};
         route_sub(s, a.plan, a.small_max_m, a.lists.big[0], a.lists.big_count[0], a.lists.big_cap,
-                  a.lists.small, a.lists.small_count, a.lists.medium, a.lists.medium_count, a.lists.small_cap,
+                  a.lists.small, a.lists.small_count, a.lists.medium, a.lists.medium_count, a.lists.small_cap, a.lists.medium_cap,
                   a.lists.bigfy, a.lists.bigfy_count, a.lists.bigfy_cap, a.status);
     }
 }
@@ -226,7 +226,7 @@ __global__ void scan_kernel(LevelArgs a, uint32_t small_max_m) {
             a.child[(uint64_t)wi * k + b] = ci;
             const Sub c{ci.o, ci.m, S.arr, S.level + 1, ci.eps, 0};
             route_sub(c, a.plan, small_max_m, a.next_big, a.next_big_count, a.big_cap, a.small, a.small_count,
-                      a.medium, a.medium_count, a.small_cap, a.bigfy, a.bigfy_count, a.bigfy_cap, a.status);
+                      a.medium, a.medium_count, a.small_cap, a.medium_cap, a.bigfy, a.bigfy_count, a.bigfy_cap, a.status);
         }
         __syncthreads();
     }

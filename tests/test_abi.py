@@ -70,6 +70,17 @@ def test_default_plan_and_workspace_size_on_host():
     assert rip.rip_shuffle_workspace_size(100, 4, nested_bad) == 0
 
 
+def test_capacity_plan_keeps_aux_below_one_percent_at_2pow34():
+    for w in (4, 8):
+        n = 1 << 34
+        p = rip.rip_capacity_plan(n, w)
+        assert p.ks == [1024, 1024] and p.max_levels == 2 and p.Bs[0] * w == 1024 and p.Bs[1] == 32
+        ws = rip.rip_shuffle_workspace_size(n, w, p)
+        assert 0 < ws <= 0.01 * n * w
+    # the default plan at the benchmark size, for the record
+    assert rip.rip_shuffle_workspace_size(1 << 30, 8) < 0.013 * (1 << 30) * 8
+
+
 def test_oracle_and_library_share_no_code():
     """The oracle (test infrastructure) and the CUDA sources include nothing of each other."""
     csrc = os.path.join(ROOT, "paper_2302_03317_gb300", "csrc")

@@ -390,3 +390,31 @@ def test_threaded_children_equal_sequential(plan):
     got = a.copy()
     oracle.shuffle_parallel(got, 17, plan, threads=4)
     assert np.array_equal(got, want)
+
+
+# --- streaming evaluation of the root level (checks of near-capacity runs) --------------
+
+@pytest.mark.parametrize("w", [4, 8])
+@pytest.mark.parametrize("T,budget", [(1 << 15, 1 << 40), (1001, 5000), (4096, 1 << 16)])
+def test_streaming_root_matches_plain_oracle(w, T, budget):
+    """Digest and sampled ranges of the piecewise root level + per-bucket recursion equal those
+    of the plain out-of-place oracle, with bucket groups forced small and tiles that cut
+    Philox quads (T odd)."""
+    dt = np.uint32 if w == 4 else np.uint64
+    Bs = [7, 7] if T % 32 else [32, 8]
+    p = oracle.Plan([64, 16], [T, Bs[1] << 17], Bs, 300, 2)
+    n = 200_003
+    want = oracle.shuffle(np.arange(n, dtype=dt), 11, p)
+    ranges = [(0, 1000), (n - 777, 777), (100_000, 50_000), (12_345, 1)]
+    h, got = oracle.iota_digest_and_ranges(n, w, 11, p, ranges, threads=3, budget_bytes=budget)
+    assert h == oracle.digest(want)
+    for (r0, rl), g in zip(ranges, got):
+        assert np.array_equal(g, want[r0:r0 + rl])
+
+
+def test_digest_is_a_sum_over_pieces():
+    a = np.arange(10_000, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15)
+    lib = oracle._load()
+    parts = [(0, 1), (1, 4000), (4000, 10_000)]
+    h = sum(int(lib.oracle_hash_at(a[x:y].ctypes.data, y - x, 8, x)) for x, y in parts) & (2**64 - 1)
+    assert h == oracle.digest(a)
