@@ -179,6 +179,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-log2", type=int, default=26)
     ap.add_argument("--ref-sample-log2", type=int, default=22)
+    ap.add_argument("--workload", choices=["default", "capacity-u32", "capacity-u64"], default="default",
+                    help="capacity-*: 2^34 elements (64 / 128 GiB) with rip_capacity_plan (k = 1024, two levels)")
     ap.add_argument("--ks", type=str, default="", help="profiling: comma list of k per level (overrides the default plan)")
     ap.add_argument("--Bs", type=str, default="", help="profiling: comma list of B per level")
     ap.add_argument("--Ts", type=str, default="", help="profiling: comma list of T per level")
@@ -203,16 +205,24 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    n = 1 << args.log2n
-    w = ELEM_BYTES
-    plan = rip.rip_default_plan(n, w)
+    capacity = args.workload != "default"
+    n = 1 << (34 if capacity else args.log2n)
+    w = 4 if args.workload == "capacity-u32" else ELEM_BYTES
+    dtype_name = "u32" if w == 4 else "u64"
+    plan = rip.rip_capacity_plan(n, w) if capacity else rip.rip_default_plan(n, w)
     if args.ks:
         ks = [int(v) for v in args.ks.split(",")]
         Bs = [int(v) for v in args.Bs.split(",")] if args.Bs else [128 * 1024 // (k * w) for k in ks]
         Ts = [int(v) for v in args.Ts.split(",")] if args.Ts else [(1 << 26) // b * b for b in Bs]
         plan = rip.Plan(ks=ks, Ts=Ts, Bs=Bs, base=plan.base, max_levels=0)
-    x = torch.empty(n, dtype=torch.int64, device="cuda")
-    fill_iota_(x, w)
+    x = torch.empty(n, dtype=torch.int32 if w == 4 else torch.int64, device="cuda")
+    if w == 4:  # iota mod 2^32, filled in pieces (no full-size temporary)
+        for s0 in range(0, n, 1 << 30):
+            v = torch.arange(s0, min(n, s0 + (1 << 30)), dtype=torch.int64, device="cuda") & 0xFFFFFFFF
+            x[s0:s0 + v.shape[0]] = torch.where(v >= (1 << 31), v - (1 << 32), v).to(torch.int32)
+            del v
+    else:
+        fill_iota_(x, w)
     stream = torch.cuda.current_stream()
 
     for i in range(args.warmup):
@@ -275,7 +285,7 @@ def main():
 
     # end to end through the C ABI: pinned host array -> device, shuffle, -> host
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not capacity:
         host = torch.empty(n, dtype=torch.int64, pin_memory=True)
         host.copy_(x)
         torch.cuda.synchronize()
@@ -296,7 +306,7 @@ def main():
         del host
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and not capacity:
         rate, dt, ns = cpu_oracle_sample(plan, args.cpu_sample_log2)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"2^{args.cpu_sample_log2} u64 iota with the same plan (one shuffle, {dt:.1f} s)"}
@@ -305,14 +315,15 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": f"in-place shuffle of 2^{args.log2n} u64 iota per GPU, default plan",
+            "vs_baseline": None, "dtype": dtype_name, "data": "synthetic",
+            "config": {"workload": (f"near-capacity in-place shuffle of 2^34 {dtype_name} iota per GPU, capacity plan"
+                                    if capacity else f"in-place shuffle of 2^{args.log2n} u64 iota per GPU, default plan"),
                        "n": n, "elem_bytes": w, "seed": SEED,
                        "plan": {"k": list(plan.ks), "T": list(plan.Ts), "B": list(plan.Bs), "base": plan.base,
                                 "max_levels": plan.max_levels},
                        "inplace_levels": info["inplace_levels"], "aux_bytes": info["aux_bytes"],
                        "aux_frac": info["aux_bytes"] / (n * w),
-                       "l2": "inputs larger than L2 (8 GiB array vs 129 MB L2)",
+                       "l2": f"inputs larger than L2 ({n * w / 2**30:.0f} GiB array vs 129 MB L2)",
                        "parallelism": f"replicas{ws}" if ws > 1 else "single"},
             "roofline": roof,
             "whole_shuffle_roofline_frac": whole_roof_ms / ms_per_step,
