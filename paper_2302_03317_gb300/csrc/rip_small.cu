@@ -146,6 +146,62 @@ __device__ void fy_parallel(uint16_t* Z, uint16_t* H, uint32_t* R, uint32_t len,
 
 // Fisher-Yates over Z[0..len) with the partner draws computed by the whole
 // block into `draws` first; the dependent swap chain then runs on thread 0.
+// 16-bit atomic maximum on shared memory, by compare-and-swap on the containing word.
+__device__ __forceinline__ void atomic_max_u16(uint16_t* addr, uint32_t val) {
+    uint32_t* word = reinterpret_cast<uint32_t*>(reinterpret_cast<uintptr_t>(addr) & ~uintptr_t(3));
+    const uint32_t shift = (reinterpret_cast<uintptr_t>(addr) & 2u) ? 16u : 0u;
+    uint32_t old = *word;
+    for (;;) {
+        if (((old >> shift) & 0xFFFFu) >= val) return;
+        const uint32_t nv = (old & ~(0xFFFFu << shift)) | (val << shift);
+        const uint32_t prev = atomicCAS(word, old, nv);
+        if (prev == old) return;
+        old = prev;
+    }
+}
+
+// Fisher-Yates of a leaf of up to 2^15 elements, on the elements themselves, with the same
+// deterministic reservations as fy_parallel (every round commits each remaining step that is
+// the latest of all remaining steps touching both of its positions; the sequential order's
+// result): partner draws in H (bit 15 marks a step done), 16-bit reservations in R.
+template <typename T>
+__device__ void fy_parallel_data(T* D, uint16_t* H, uint16_t* R, uint32_t len, Status* status) {
+    __shared__ uint32_t remaining;
+    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) R[i] = 0;
+    if (threadIdx.x == 0) H[0] = 0x8000u;  // step 0 does nothing
+    for (uint32_t round = 0;; ++round) {
+        __syncthreads();
+        if (threadIdx.x == 0) remaining = 0;
+        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
+            const uint32_t h = H[i];
+            if (h & 0x8000u) continue;
+            atomic_max_u16(&R[i], i);
+            atomic_max_u16(&R[h], i);
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
+            const uint32_t h = H[i];
+            if (h & 0x8000u) continue;
+            if (R[i] == i && R[h] == i) {
+                const T di = D[i];
+                D[i] = D[h];
+                D[h] = di;
+                H[i] = (uint16_t)(h | 0x8000u);
+            } else {
+                remaining = 1;
+            }
+        }
+        __syncthreads();
+        if (!remaining) break;
+        if (round > 4 * len) {  // cannot happen: the largest unfinished step always commits
+            if (threadIdx.x == 0) report(status, RIP_EINTERNAL, 0x5108, len);
+            break;
+        }
+        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) R[i] = 0;
+    }
+    __syncthreads();
+}
+
 __device__ void fy_block(uint16_t* Z, uint16_t* draws, uint32_t len, PhiloxKey key, uint32_t L,
                          uint64_t leaf_o) {
     for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
@@ -523,10 +579,15 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(SmallArgs args) {
         if (tid == 0) sh.stack_top = 0;
         __syncthreads();
 
+        bool in_place = false;  // D already holds the output order
         if (plan.is_leaf(m, s.level)) {
             if (m > 1 && m <= kParallelFyMax) {
                 fy_draws(P1, m, key, s.level, s.o);
                 fy_parallel(P0, P1, sh.g.thr, m, args.status);
+            } else if (m > 1 && m <= 0x8000u) {
+                fy_draws(P1, m, key, s.level, s.o);
+                fy_parallel_data(D, P1, P0, m, args.status);  // P0 holds the reservations
+                in_place = true;
             } else if (m > 1) {
                 fy_block(P0, P1, m, key, s.level, s.o);
             }
@@ -561,10 +622,14 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(SmallArgs args) {
             }
         }
         __syncthreads();
-        for (uint32_t i = tid; i < m; i += blockDim.x) {
-            const uint32_t j = P0[i];
-            if (j < m) base[s.o + i] = D[j];
-            else report(args.status, RIP_EINTERNAL, 0x5107, j);  // never read outside the subproblem
+        if (in_place) {
+            for (uint32_t i = tid; i < m; i += blockDim.x) base[s.o + i] = D[i];
+        } else {
+            for (uint32_t i = tid; i < m; i += blockDim.x) {
+                const uint32_t j = P0[i];
+                if (j < m) base[s.o + i] = D[j];
+                else report(args.status, RIP_EINTERNAL, 0x5107, j);  // never read outside the subproblem
+            }
         }
         __syncthreads();
     }
