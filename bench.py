@@ -34,6 +34,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "shuffled elems/s and % HBM roofline (2^30 u64); batched vs plain elems/s"
+# dram__bytes_read + dram__bytes_write per element of one launch, from the ncu captures
+# summarised in profiles/classify_shuffle_2pow26_u64.md and profiles/permute_shuffle_2pow26_u64.md
+DRAM_BYTES_PER_ELEM = {"classify": 13.3, "permute": 13.5}
 UNIT = "elems/s"
 N_LOG2 = 30
 ELEM_BYTES = 8
@@ -260,20 +263,27 @@ def main():
     ms_per_step = t_max / args.steps
     value = job_rate(ws, n, ms_per_step)
 
-    # roofline of the dominant kernel: algorithmic bytes = one read + one write of
-    # every element the launch processes (each of these kernels touches the whole
-    # array once per launch for this workload)
+    # roofline of the dominant kernel: algorithmic bytes = one read + one write of every
+    # element a launch processes.  Per shuffle, classify and permute process every element
+    # once per in-place level (a level may run in several waves, i.e. launches), the solver
+    # every element once; per launch = that total / launches.
     hbm_gbs, peak_kind = _measured_hbm_gbs()
     heavy = {k: v for k, v in prof.items() if k in ("classify", "permute", "solve_small", "solve_medium")}
     dom = max(heavy.items(), key=lambda kv: kv[1][1]) if heavy else None
     roof = None
     if dom:
         name, (launches, total_ms) = dom
+        per_step = launches / args.steps
+        elems_step = n * (info["inplace_levels"] if name in ("classify", "permute") else 1)
         avg_ms = total_ms / max(launches, 1)
-        alg_bytes = 2 * n * w
+        alg_bytes = 2 * w * elems_step / max(per_step, 1)
         achieved = alg_bytes / (avg_ms / 1e3) / 1e9
+        # DRAM bytes per element from the ncu captures in profiles/ (2^26 u64, default plan),
+        # scaled to this launch; only for the default workload they were measured on
+        per_elem = DRAM_BYTES_PER_ELEM.get(name) if not capacity and w == 8 else None
+        traffic = per_elem * alg_bytes / (2 * w) if per_elem else None
         roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s",
-                "frac": achieved / hbm_gbs, "traffic": None, "peak_kind": peak_kind,
+                "frac": achieved / hbm_gbs, "traffic": traffic, "peak_kind": peak_kind,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms}
     # whole-shuffle roofline: one read + one write per scatter level plus one for Fisher-Yates
     scatter_levels, m_exp = 0, float(n)

@@ -157,6 +157,7 @@ struct SmallArgs {
     char* gscratch;
     uint64_t gslot_bytes;
     uint32_t medium;
+    uint32_t dyn_bytes;  // dynamic shared memory after SmallShared (set by launch_small)
 };
 
 constexpr uint32_t kInlineArrays = 4;

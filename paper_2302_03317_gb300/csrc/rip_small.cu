@@ -16,8 +16,6 @@ namespace rip {
 namespace {
 
 constexpr uint32_t kThreads = kSmallThreads;
-// leaves up to this size use the parallel Fisher-Yates; its reservation words
-// live in the general scratch area (sizeof(GeneralScratch) / 4 words)
 constexpr uint32_t kWarps = kThreads / 32;
 
 struct GeneralScratch {         // scatter of a range with several tiles or k > 256
@@ -32,8 +30,6 @@ struct FastScratch {               // single-tile scatter with k <= 256
     uint32_t start[256];           // per bucket: total, then first output index of the bucket
     uint32_t mask[kWarps * 64];    // per (warp, low 6 bucket bits): lanes of the current step
 };
-
-constexpr uint32_t kParallelFyMax = (uint32_t)(sizeof(GeneralScratch) / sizeof(uint32_t));
 
 struct SmallShared {
     union {
@@ -100,52 +96,6 @@ __device__ void fy_draws(uint16_t* H, uint32_t len, PhiloxKey key, uint32_t L, u
     __syncthreads();
 }
 
-// Fisher-Yates over Z[0..len) in parallel with the same result as the sequential
-// loop for the same draws (deterministic reservations; Shun, Gu, Blelloch,
-// Fineman, Gibbons, SODA 2015, which the paper cites for parallel Fisher-Yates):
-// step i swaps positions i and H[i] <= i and must follow every larger step that
-// touches either position.  Each round, every unfinished step writes its index
-// into both positions' reservation word with atomicMax; a step holding both
-// reservations performs its swap.  H's top bit marks finished steps; len < 2^15.
-__device__ void fy_parallel(uint16_t* Z, uint16_t* H, uint32_t* R, uint32_t len, Status* status) {
-    __shared__ uint32_t remaining;
-    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) R[i] = 0;
-    if (threadIdx.x == 0) H[0] = 0x8000u;  // step 0 does nothing
-    for (uint32_t round = 0;; ++round) {
-        __syncthreads();
-        if (threadIdx.x == 0) remaining = 0;
-        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
-            const uint32_t h = H[i];
-            if (h & 0x8000u) continue;
-            atomicMax(&R[i], i);
-            atomicMax(&R[h], i);
-        }
-        __syncthreads();
-        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
-            const uint32_t h = H[i];
-            if (h & 0x8000u) continue;
-            if (R[i] == i && R[h] == i) {
-                const uint16_t zi = Z[i];
-                Z[i] = Z[h];
-                Z[h] = zi;
-                H[i] = (uint16_t)(h | 0x8000u);
-            } else {
-                remaining = 1;
-            }
-        }
-        __syncthreads();
-        if (!remaining) break;
-        if (round > 4 * len) {  // cannot happen: the largest unfinished step always commits
-            if (threadIdx.x == 0) report(status, RIP_EINTERNAL, 0x5106, len);
-            break;
-        }
-        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) R[i] = 0;
-    }
-    __syncthreads();
-}
-
-// Fisher-Yates over Z[0..len) with the partner draws computed by the whole
-// block into `draws` first; the dependent swap chain then runs on thread 0.
 // 16-bit atomic maximum on shared memory, by compare-and-swap on the containing word.
 __device__ __forceinline__ void atomic_max_u16(uint16_t* addr, uint32_t val) {
     uint32_t* word = reinterpret_cast<uint32_t*>(reinterpret_cast<uintptr_t>(addr) & ~uintptr_t(3));
@@ -160,44 +110,60 @@ __device__ __forceinline__ void atomic_max_u16(uint16_t* addr, uint32_t val) {
     }
 }
 
-// Fisher-Yates of a leaf of up to 2^15 elements, on the elements themselves, with the same
-// deterministic reservations as fy_parallel (every round commits each remaining step that is
-// the latest of all remaining steps touching both of its positions; the sequential order's
-// result): partner draws in H (bit 15 marks a step done), 16-bit reservations in R.
-template <typename T>
-__device__ void fy_parallel_data(T* D, uint16_t* H, uint16_t* R, uint32_t len, Status* status) {
+__device__ __forceinline__ void atomic_max_r(uint16_t* addr, uint32_t val) { atomic_max_u16(addr, val); }
+__device__ __forceinline__ void atomic_max_r(uint32_t* addr, uint32_t val) { atomicMax(addr, val); }
+
+// Fisher-Yates of a leaf of up to 2^15 elements on the elements themselves, by deterministic
+// reservations (Shun, Gu, Blelloch, Fineman, Gibbons, SODA 2015): every round commits each
+// unfinished step that is the latest of all unfinished steps touching either of its two
+// positions, which gives the sequential order's result.  Partner draws in H, reservations in R (16- or 32-bit); thread
+// t owns steps t + j*blockDim and keeps the unfinished ones in a 64-bit mask, so a round
+// touches only unfinished steps.
+template <typename T, typename RT>
+__device__ void fy_parallel_data(T* D, const uint16_t* H, RT* R, uint32_t len, Status* status) {
     __shared__ uint32_t remaining;
-    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) R[i] = 0;
-    if (threadIdx.x == 0) H[0] = 0x8000u;  // step 0 does nothing
+    const uint32_t nb = blockDim.x, tid = threadIdx.x;
+    uint64_t mine = 0;
+    for (uint32_t j = 0; j < 64u && tid + j * nb < len; ++j)
+        if (tid + j * nb >= 1u) mine |= 1ull << j;  // step 0 does nothing
+    for (uint32_t i = tid; i < len; i += nb) R[i] = 0;
     for (uint32_t round = 0;; ++round) {
         __syncthreads();
-        if (threadIdx.x == 0) remaining = 0;
-        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
+        if (tid == 0) remaining = 0;
+        for (uint64_t mk = mine; mk; mk &= mk - 1) {
+            const uint32_t i = tid + (uint32_t)(__ffsll((long long)mk) - 1) * nb;
             const uint32_t h = H[i];
-            if (h & 0x8000u) continue;
-            atomic_max_u16(&R[i], i);
-            atomic_max_u16(&R[h], i);
+            atomic_max_r(&R[i], i);
+            atomic_max_r(&R[h], i);
         }
         __syncthreads();
-        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
+        uint64_t left = 0;
+        for (uint64_t mk = mine; mk; mk &= mk - 1) {
+            const uint32_t j = (uint32_t)(__ffsll((long long)mk) - 1);
+            const uint32_t i = tid + j * nb;
             const uint32_t h = H[i];
-            if (h & 0x8000u) continue;
             if (R[i] == i && R[h] == i) {
                 const T di = D[i];
                 D[i] = D[h];
                 D[h] = di;
-                H[i] = (uint16_t)(h | 0x8000u);
             } else {
-                remaining = 1;
+                left |= 1ull << j;
             }
         }
+        if (left) remaining = 1;
         __syncthreads();
-        if (!remaining) break;
-        if (round > 4 * len) {  // cannot happen: the largest unfinished step always commits
-            if (threadIdx.x == 0) report(status, RIP_EINTERNAL, 0x5108, len);
+        const bool again = remaining != 0;
+        for (uint64_t mk = mine; mk; mk &= mk - 1) {  // clear what this round reserved
+            const uint32_t i = tid + (uint32_t)(__ffsll((long long)mk) - 1) * nb;
+            R[i] = 0;
+            R[H[i]] = 0;
+        }
+        mine = left;
+        if (!again) break;
+        if (round > 4 * len) {  // cannot happen: the latest unfinished step always commits
+            if (tid == 0) report(status, RIP_EINTERNAL, 0x5108, len);
             break;
         }
-        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) R[i] = 0;
     }
     __syncthreads();
 }
@@ -581,12 +547,15 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(SmallArgs args) {
 
         bool in_place = false;  // D already holds the output order
         if (plan.is_leaf(m, s.level)) {
-            if (m > 1 && m <= kParallelFyMax) {
+            if (m > 1 && m <= 64u * kThreads) {
                 fy_draws(P1, m, key, s.level, s.o);
-                fy_parallel(P0, P1, sh.g.thr, m, args.status);
-            } else if (m > 1 && m <= 0x8000u) {
-                fy_draws(P1, m, key, s.level, s.o);
-                fy_parallel_data(D, P1, P0, m, args.status);  // P0 holds the reservations
+                // 32-bit reservations after D when they fit, else 16-bit ones in P0's place
+                const uint64_t mr = (m + 7u) & ~7u;
+                const uint64_t r32_off = 4 * mr + (args.medium ? 0 : (uint64_t)W * mr);
+                if (r32_off + 4 * mr <= args.dyn_bytes)
+                    fy_parallel_data(D, P1, reinterpret_cast<uint32_t*>(dyn + r32_off), m, args.status);
+                else
+                    fy_parallel_data(D, P1, P0, m, args.status);
                 in_place = true;
             } else if (m > 1) {
                 fy_block(P0, P1, m, key, s.level, s.o);
@@ -644,8 +613,10 @@ size_t small_smem_bytes(uint64_t m, uint32_t w, bool medium) {
     return small_fixed_smem() + 4 * mr + (medium ? 0 : w * mr);
 }
 
-cudaError_t launch_small(const SmallArgs& args, uint32_t w, size_t smem, uint32_t grid, cudaStream_t stream) {
+cudaError_t launch_small(const SmallArgs& args_in, uint32_t w, size_t smem, uint32_t grid, cudaStream_t stream) {
     cudaError_t err;
+    SmallArgs args = args_in;
+    args.dyn_bytes = (uint32_t)(smem - small_fixed_smem());
     ProfScope p(args.medium ? "solve_medium" : "solve_small", stream);
     switch (w) {
         case 4:
