@@ -171,6 +171,93 @@ def run_reference(args):
     return 0
 
 
+def run_batched(args, rip, torch, dist, ws, rank, local, barrier):
+    """Many independent shuffles: one rip_shuffle_batched call per step (each array its own
+    default plan) against one rip_shuffle call per array; same seeds, same results."""
+    from paper_2302_03317_gb300.inputs import batched_sizes
+    sizes = [int(v) for v in batched_sizes(args.arrays, seed=SEED)]
+    offs, o = [], 0
+    for n in sizes:  # every array starts 16-byte aligned inside one allocation
+        offs.append(o)
+        o += (n + 3) // 4 * 4
+    buf = torch.empty(o, dtype=torch.int32, device="cuda")
+    views = [buf[a:a + n] for a, n in zip(offs, sizes)]
+    for v in views:
+        v.copy_(torch.arange(v.shape[0], dtype=torch.int32, device="cuda"))
+    total = sum(sizes)
+    stream = torch.cuda.current_stream()
+
+    def batched(seed):
+        rip.shuffle_batched_(views, seed)
+
+    def plain(seed):
+        for i, v in enumerate(views):
+            rip.shuffle_(v, seed + i)
+
+    for i in range(args.warmup):
+        batched(SEED + i)
+    plain(SEED)
+    rc = rip.rip_get_device_status(stream.cuda_stream)
+    if rc != 0:
+        raise SystemExit(f"device status after warm-up: {rip.rip_strerror(rc)}")
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    rip.rip_profile_reset()
+    rip.rip_profile_enable(True)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        batched(SEED + 100 * (i + 1))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    rip.rip_profile_enable(False)
+    prof = rip.rip_profile_get()
+    launches = sum(v[0] for v in prof.values())
+    ms_b = max_over_ranks(e0.elapsed_time(e1), dist, "cuda") / args.steps
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    plain(SEED + 7)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms_p = max_over_ranks(p0.elapsed_time(p1), dist, "cuda")
+    rc = rip.rip_get_device_status(stream.cuda_stream)
+    if rc != 0:
+        raise SystemExit(f"device status after timed steps: {rip.rip_strerror(rc)}")
+    value = job_rate(ws, total, ms_b)
+    plain_rate = job_rate(ws, total, ms_p)
+    hbm_gbs, peak_kind = _measured_hbm_gbs()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"batched: {args.arrays} u32 iota arrays, sizes log-uniform in [2^8, 2^20] "
+                                   f"(numpy default_rng({SEED})), seed base_seed + i, default plan per array",
+                       "arrays": args.arrays, "elements": total, "elem_bytes": 4,
+                       "l2": f"{total * 4 / 2**30:.1f} GiB of arrays vs 129 MB L2",
+                       "parallelism": f"replicas{ws}" if ws > 1 else "single"},
+            "plain": {"value": plain_rate, "unit": UNIT, "ms_per_step": ms_p,
+                      "how": "one rip_shuffle call per array, same seeds and results"},
+            "vs_plain": value / plain_rate,
+            "roofline": {"bound": "hbm", "kernel": "whole batched call", "achieved": 2 * 4 * total / (ms_b / 1e3) / 1e9,
+                         "peak": hbm_gbs, "unit": "GB/s",
+                         "frac": 2 * 4 * total / (ms_b / 1e3) / 1e9 / hbm_gbs, "traffic": None,
+                         "peak_kind": peak_kind, "note": "one read + one write of every element per call"},
+            "kernels": {k: {"launches": v[0], "ms_per_step": v[1] / args.steps} for k, v in sorted(prof.items())},
+            "cpu_baseline": None, "e2e": None,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -182,8 +269,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-log2", type=int, default=26)
     ap.add_argument("--ref-sample-log2", type=int, default=22)
-    ap.add_argument("--workload", choices=["default", "capacity-u32", "capacity-u64"], default="default",
-                    help="capacity-*: 2^34 elements (64 / 128 GiB) with rip_capacity_plan (k = 1024, two levels)")
+    ap.add_argument("--workload", choices=["default", "capacity-u32", "capacity-u64", "batched"], default="default",
+                    help="capacity-*: 2^34 elements (64 / 128 GiB) with rip_capacity_plan (k = 1024, two levels); "
+                         "batched: 4096 u32 arrays, sizes log-uniform in [2^8, 2^20], one batched call vs one call per array")
+    ap.add_argument("--arrays", type=int, default=4096)
     ap.add_argument("--ks", type=str, default="", help="profiling: comma list of k per level (overrides the default plan)")
     ap.add_argument("--Bs", type=str, default="", help="profiling: comma list of B per level")
     ap.add_argument("--Ts", type=str, default="", help="profiling: comma list of T per level")
@@ -208,6 +297,8 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    if args.workload == "batched":
+        return run_batched(args, rip, torch, dist, ws, rank, local, barrier)
     capacity = args.workload != "default"
     n = 1 << (34 if capacity else args.log2n)
     w = 4 if args.workload == "capacity-u32" else ELEM_BYTES

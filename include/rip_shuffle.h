@@ -117,14 +117,26 @@ int rip_shuffle_ex(void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed,
 
 /* Batched form (Sec. 6, many independent shuffles): array i (device pointer
  * ptrs[i], ns[i] elements) is shuffled with seed base_seed + i, positions
- * relative to its own start, all arrays with the same plan (NULL = default
- * plan for the largest array).  ptrs and ns are HOST arrays of `count`
- * entries; the arrays must not overlap.  ws as in rip_shuffle_ex. */
+ * relative to its own start.  plan != NULL: every array uses it; plan ==
+ * NULL: every array uses its own default plan (rip_default_plan(ns[i])), so an
+ * array's result is the same alone and in any batch.  Arrays that share a plan
+ * run together: one level-synchronous pass over all of them, the small ones on
+ * one SM each; groups with different plans run one after another on `stream`.
+ * ptrs and ns are HOST arrays of `count` entries; the arrays must not overlap.
+ * ws as in rip_shuffle_ex (the workspace is the largest any group needs). */
 size_t rip_shuffle_batched_workspace_size(const uint64_t *ns, uint32_t count, uint32_t elem_bytes,
                                           const rip_plan *plan);
 int rip_shuffle_batched(void *const *ptrs, const uint64_t *ns, uint32_t count, uint32_t elem_bytes,
                         uint64_t base_seed, const rip_plan *plan, void *ws, size_t ws_bytes,
                         rip_stream_t stream);
+
+/* Batched form with one plan per array (plans: HOST array of `count` plans,
+ * e.g. chosen per size class by a tuner); otherwise as rip_shuffle_batched. */
+size_t rip_shuffle_batched_plans_workspace_size(const uint64_t *ns, uint32_t count, uint32_t elem_bytes,
+                                                const rip_plan *plans);
+int rip_shuffle_batched_plans(void *const *ptrs, const uint64_t *ns, uint32_t count, uint32_t elem_bytes,
+                              uint64_t base_seed, const rip_plan *plans, void *ws, size_t ws_bytes,
+                              rip_stream_t stream);
 
 /* Position-dependent 64-bit digest of data[0..n), computed on the device:
  *   H = sum_p splitmix64(p * 0x9E3779B97F4A7C15 ^ v(p)) mod 2^64,

@@ -102,6 +102,11 @@ def _load():
         lib.rip_shuffle_batched_workspace_size.restype = sz
         lib.rip_shuffle_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(u64), u32, u32, u64, pplan, vp, sz, vp]
         lib.rip_shuffle_batched.restype = i32
+        lib.rip_shuffle_batched_plans_workspace_size.argtypes = [ctypes.POINTER(u64), u32, u32, pplan]
+        lib.rip_shuffle_batched_plans_workspace_size.restype = sz
+        lib.rip_shuffle_batched_plans.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(u64), u32, u32, u64, pplan,
+                                                  vp, sz, vp]
+        lib.rip_shuffle_batched_plans.restype = i32
         lib.rip_digest.argtypes = [vp, u64, u32, ctypes.POINTER(u64), vp]
         lib.rip_digest.restype = i32
         lib.rip_get_device_status.argtypes = [vp]
@@ -184,6 +189,27 @@ def rip_shuffle_batched(ptrs: Sequence[int], ns: Sequence[int], elem_bytes: int,
     narr = (ctypes.c_uint64 * count)(*ns)
     _check(_load().rip_shuffle_batched(parr, narr, count, elem_bytes, base_seed, _plan_ptr(plan), ws_ptr or None,
                                        ws_bytes, stream), "rip_shuffle_batched")
+
+
+def _plan_array(plans):
+    arr = (rip_plan * len(plans))()
+    for i, p in enumerate(plans):
+        arr[i] = p.to_c() if isinstance(p, Plan) else p
+    return arr
+
+
+def rip_shuffle_batched_plans_workspace_size(ns: Sequence[int], elem_bytes: int, plans) -> int:
+    arr = (ctypes.c_uint64 * len(ns))(*ns)
+    return int(_load().rip_shuffle_batched_plans_workspace_size(arr, len(ns), elem_bytes, _plan_array(plans)))
+
+
+def rip_shuffle_batched_plans(ptrs: Sequence[int], ns: Sequence[int], elem_bytes: int, base_seed: int, plans,
+                              ws_ptr: int = 0, ws_bytes: int = 0, stream: int = 0) -> None:
+    count = len(ptrs)
+    parr = (ctypes.c_void_p * count)(*ptrs)
+    narr = (ctypes.c_uint64 * count)(*ns)
+    _check(_load().rip_shuffle_batched_plans(parr, narr, count, elem_bytes, base_seed, _plan_array(plans),
+                                             ws_ptr or None, ws_bytes, stream), "rip_shuffle_batched_plans")
 
 
 def rip_digest(data_ptr: int, n: int, elem_bytes: int, stream: int = 0) -> int:
@@ -279,8 +305,12 @@ def shuffle_batched_(tensors, base_seed: int, plan=None, ws=None, stream=None, c
     if any(elem_bytes_of(t) != w for t in tensors):
         raise ValueError("all arrays of a batch need the same element width")
     ws_ptr, ws_bytes = (ws.data_ptr(), ws.numel() * ws.element_size()) if ws is not None else (0, 0)
-    rip_shuffle_batched([t.data_ptr() for t in tensors], [t.shape[0] for t in tensors], w, base_seed, plan,
-                        ws_ptr, ws_bytes, _stream_handle(stream))
+    if isinstance(plan, (list, tuple)):  # one plan per array
+        rip_shuffle_batched_plans([t.data_ptr() for t in tensors], [t.shape[0] for t in tensors], w, base_seed,
+                                  plan, ws_ptr, ws_bytes, _stream_handle(stream))
+    else:
+        rip_shuffle_batched([t.data_ptr() for t in tensors], [t.shape[0] for t in tensors], w, base_seed, plan,
+                            ws_ptr, ws_bytes, _stream_handle(stream))
     if check:
         _check(rip_get_device_status(_stream_handle(stream)), "device")
     return tensors

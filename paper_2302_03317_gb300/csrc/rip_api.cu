@@ -443,8 +443,10 @@ DevState* dev_state(int* dev_out) {
     return &d;
 }
 
-int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns, uint32_t w, uint64_t base_seed,
-                const rip_plan* plan_in, void* ws, size_t ws_bytes, cudaStream_t stream) {
+// One level-synchronous run over arrays that share a plan: array i is shuffled with seeds[i].
+// Adds to the device's last-call diagnostics (callers clear them).
+int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns, const std::vector<uint64_t>& seeds,
+                uint32_t w, const rip_plan& plan, void* ws, size_t ws_bytes, cudaStream_t stream) {
     if (!valid_w(w)) return RIP_EINVAL;
     for (size_t i = 0; i < ptrs.size(); ++i) {
         if (ns[i] > 1 && !ptrs[i]) return RIP_EINVAL;
@@ -454,15 +456,9 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
     int dev = 0;
     DevState* ds = dev_state(&dev);
     if (!ds) return RIP_ECUDA;
-    uint64_t nmax = 0;
-    for (uint64_t n : ns) nmax = std::max(nmax, n);
-    rip_plan plan;
-    if (plan_in) plan = *plan_in;
-    else default_plan_impl(nmax, w, &plan, ds->num_sms);
     if (validate_plan(plan, w) != RIP_OK) return RIP_EINVAL;
     bool any = false;
     for (uint64_t n : ns) any |= n > 1;
-    ds->last_info[0] = ds->last_info[1] = ds->last_info[2] = 0;
     if (!any) return RIP_OK;
 
     const Layout lay = make_layout(ns, w, plan);
@@ -486,7 +482,7 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
         }
         wsp = static_cast<char*>(ds->ws);
     }
-    ds->last_info[0] = lay.aux_bytes;
+    ds->last_info[0] = std::max<uint64_t>(ds->last_info[0], lay.aux_bytes);
 
     const DevPlan dplan = to_dev(plan);
     // tuning knob: chain steps before the permutation parks a block (RIP_PARK_AFTER)
@@ -496,7 +492,7 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
     std::vector<ArrayDesc> arr(ptrs.size());
     bool aligned16 = true;
     for (size_t i = 0; i < ptrs.size(); ++i) {
-        arr[i] = ArrayDesc{ptrs[i], ns[i] > 1 ? ns[i] : 0, base_seed + i};
+        arr[i] = ArrayDesc{ptrs[i], ns[i] > 1 ? ns[i] : 0, seeds[i]};
         aligned16 &= (reinterpret_cast<uintptr_t>(ptrs[i]) % 16) == 0;
     }
     ArrayDesc* d_arr = reinterpret_cast<ArrayDesc*>(wsp + lay.arrays);
@@ -621,8 +617,89 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
                      lists.big_count[lay.levels & 1], ds->status, stream) != cudaSuccess)
         return RIP_ECUDA;
     ++launches;
-    ds->last_info[1] = lay.levels;
-    ds->last_info[2] = launches;
+    ds->last_info[1] = std::max<uint64_t>(ds->last_info[1], lay.levels);
+    ds->last_info[2] += launches;
+    return RIP_OK;
+}
+
+// Arrays grouped by their plan (one run per group): `uniform` for every array if given,
+// else plans[i] if given, else the default plan of each array's own size.
+struct Group {
+    rip_plan plan;
+    std::vector<uint32_t> idx;
+};
+
+bool same_plan(const rip_plan& a, const rip_plan& b) {
+    if (a.num_levels != b.num_levels || a.max_levels != b.max_levels || a.base != b.base) return false;
+    for (uint32_t l = 0; l < a.num_levels && l < RIP_MAX_LEVEL_PARAMS; ++l)
+        if (a.level[l].k != b.level[l].k || a.level[l].block != b.level[l].block || a.level[l].tile != b.level[l].tile)
+            return false;
+    return true;
+}
+
+std::vector<Group> group_arrays(const uint64_t* ns, uint32_t count, uint32_t w, const rip_plan* uniform,
+                                const rip_plan* plans, uint32_t num_sms) {
+    std::vector<Group> groups;
+    for (uint32_t i = 0; i < count; ++i) {
+        rip_plan p;
+        if (uniform) p = *uniform;
+        else if (plans) p = plans[i];
+        else default_plan_impl(ns[i], w, &p, num_sms);
+        Group* g = nullptr;
+        for (Group& x : groups)
+            if (same_plan(x.plan, p)) {
+                g = &x;
+                break;
+            }
+        if (!g) {
+            groups.push_back(Group{p, {}});
+            g = &groups.back();
+        }
+        g->idx.push_back(i);
+    }
+    return groups;
+}
+
+size_t groups_workspace(const std::vector<Group>& groups, const uint64_t* ns, uint32_t w) {
+    size_t need = 0;
+    for (const Group& g : groups) {
+        if (validate_plan(g.plan, w) != RIP_OK) return 0;
+        std::vector<uint64_t> v;
+        for (uint32_t i : g.idx) v.push_back(ns[i]);
+        need = std::max(need, make_layout(v, w, g.plan).total);
+    }
+    return need;
+}
+
+int run_groups(void* const* ptrs, const uint64_t* ns, uint32_t count, uint32_t w, uint64_t base_seed,
+               const rip_plan* uniform, const rip_plan* plans, void* ws, size_t ws_bytes, cudaStream_t stream) {
+    if (!valid_w(w)) return RIP_EINVAL;
+    if (count && (!ptrs || !ns)) return RIP_EINVAL;
+    for (uint32_t i = 0; i < count; ++i) {  // argument errors come before any device work
+        if (ns[i] > 1 && !ptrs[i]) return RIP_EINVAL;
+        if (ns[i] > 1 && (reinterpret_cast<uintptr_t>(ptrs[i]) % w)) return RIP_EINVAL;
+        if (ns[i] > (1ull << 40)) return RIP_EINVAL;
+    }
+    bool any = false;
+    for (uint32_t i = 0; i < count; ++i) any |= ns[i] > 1;
+    if (!any) return RIP_OK;
+    DevState* ds = dev_state(nullptr);
+    if (!ds) return RIP_ECUDA;
+    ds->last_info[0] = ds->last_info[1] = ds->last_info[2] = 0;
+    const std::vector<Group> groups = group_arrays(ns, count, w, uniform, plans, ds->num_sms);
+    for (const Group& g : groups)
+        if (validate_plan(g.plan, w) != RIP_OK) return RIP_EINVAL;
+    for (const Group& g : groups) {  // consecutive runs on one stream reuse the workspace
+        std::vector<char*> p;
+        std::vector<uint64_t> n, seeds;
+        for (uint32_t i : g.idx) {
+            p.push_back(static_cast<char*>(ptrs[i]));
+            n.push_back(ns[i]);
+            seeds.push_back(base_seed + i);
+        }
+        const int rc = run_shuffle(p, n, seeds, w, g.plan, ws, ws_bytes, stream);
+        if (rc) return rc;
+    }
     return RIP_OK;
 }
 
@@ -653,17 +730,17 @@ size_t rip_shuffle_workspace_size(uint64_t n, uint32_t elem_bytes, const rip_pla
 size_t rip_shuffle_batched_workspace_size(const uint64_t* ns, uint32_t count, uint32_t elem_bytes,
                                           const rip_plan* plan) {
     if (!valid_w(elem_bytes) || (count && !ns)) return 0;
-    std::vector<uint64_t> v(ns, ns + count);
-    uint64_t nmax = 0;
-    for (uint64_t n : v) nmax = std::max(nmax, n);
-    rip_plan p;
-    if (plan) p = *plan;
-    else {
-        DevState* ds = dev_state(nullptr);
-        default_plan_impl(nmax, elem_bytes, &p, ds ? ds->num_sms : 152);
-    }
-    if (validate_plan(p, elem_bytes) != RIP_OK) return 0;
-    return make_layout(v, elem_bytes, p).total;
+    DevState* ds = dev_state(nullptr);
+    return groups_workspace(group_arrays(ns, count, elem_bytes, plan, nullptr, ds ? ds->num_sms : 152), ns,
+                            elem_bytes);
+}
+
+size_t rip_shuffle_batched_plans_workspace_size(const uint64_t* ns, uint32_t count, uint32_t elem_bytes,
+                                                const rip_plan* plans) {
+    if (!valid_w(elem_bytes) || (count && (!ns || !plans))) return 0;
+    DevState* ds = dev_state(nullptr);
+    return groups_workspace(group_arrays(ns, count, elem_bytes, nullptr, plans, ds ? ds->num_sms : 152), ns,
+                            elem_bytes);
 }
 
 int rip_shuffle(void* data, uint64_t n, uint32_t elem_bytes, uint64_t seed, rip_stream_t stream) {
@@ -672,18 +749,22 @@ int rip_shuffle(void* data, uint64_t n, uint32_t elem_bytes, uint64_t seed, rip_
 
 int rip_shuffle_ex(void* data, uint64_t n, uint32_t elem_bytes, uint64_t seed, const rip_plan* plan, void* ws,
                    size_t ws_bytes, rip_stream_t stream) {
-    std::vector<char*> p{static_cast<char*>(data)};
-    std::vector<uint64_t> ns{n};
-    return run_shuffle(p, ns, elem_bytes, seed, plan, ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+    void* p[1] = {data};
+    return run_groups(p, &n, 1, elem_bytes, seed, plan, nullptr, ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int rip_shuffle_batched(void* const* ptrs, const uint64_t* ns, uint32_t count, uint32_t elem_bytes,
                         uint64_t base_seed, const rip_plan* plan, void* ws, size_t ws_bytes, rip_stream_t stream) {
-    if (count && (!ptrs || !ns)) return RIP_EINVAL;
-    std::vector<char*> p(count);
-    std::vector<uint64_t> n(ns, ns + count);
-    for (uint32_t i = 0; i < count; ++i) p[i] = static_cast<char*>(ptrs[i]);
-    return run_shuffle(p, n, elem_bytes, base_seed, plan, ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+    return run_groups(ptrs, ns, count, elem_bytes, base_seed, plan, nullptr, ws, ws_bytes,
+                      reinterpret_cast<cudaStream_t>(stream));
+}
+
+int rip_shuffle_batched_plans(void* const* ptrs, const uint64_t* ns, uint32_t count, uint32_t elem_bytes,
+                              uint64_t base_seed, const rip_plan* plans, void* ws, size_t ws_bytes,
+                              rip_stream_t stream) {
+    if (count && !plans) return RIP_EINVAL;
+    return run_groups(ptrs, ns, count, elem_bytes, base_seed, nullptr, plans, ws, ws_bytes,
+                      reinterpret_cast<cudaStream_t>(stream));
 }
 
 int rip_digest(const void* data, uint64_t n, uint32_t elem_bytes, uint64_t* out, rip_stream_t stream) {

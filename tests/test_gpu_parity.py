@@ -199,3 +199,43 @@ def test_odd_block_sizes(n, w, plan):
 ])
 def test_chunked_blocks(n, w, plan):
     check(n, w, plan, seed=5)
+
+
+def _default_oplan(n, w):
+    return _oplan(rip.rip_default_plan(n, w))
+
+
+def test_batched_default_plans_per_array_and_alone():
+    """plan=None: every array uses its own default plan (two groups here: the 6M array's
+    root tiles differ), the result equals the array shuffled alone and the oracle."""
+    sizes = [0, 1, 7, 4096, 30_000, 70_000, 1 << 20, 6_000_000]
+    arrays = [np.arange(n, dtype=np.uint32) for n in sizes]
+    ts = [_to_dev(a) for a in arrays]
+    rip.shuffle_batched_(ts, 900, plan=None, check=True)
+    for i, (t, a) in enumerate(zip(ts, arrays)):
+        got = _from_dev(t, a)
+        assert np.array_equal(got, oracle.shuffle(a, 900 + i, _default_oplan(a.shape[0], 4))), i
+        alone = _to_dev(a)
+        rip.shuffle_(alone, 900 + i, check=True)
+        assert np.array_equal(_from_dev(alone, a), got), i
+
+
+def test_batched_with_one_plan_per_array():
+    sizes = [5000, 70_000, 100_003, 300_000]
+    plans = [SMEM1, INPLACE1, INPLACE2, MIXED]
+    arrays = [np.arange(n, dtype=np.uint64) for n in sizes]
+    ts = [_to_dev(a) for a in arrays]
+    rip.shuffle_batched_(ts, 17, plan=plans, check=True)
+    for i, (t, a, p) in enumerate(zip(ts, arrays, plans)):
+        assert np.array_equal(_from_dev(t, a), oracle.shuffle(a, 17 + i, _oplan(p))), i
+
+
+def test_batched_log_uniform_sizes():
+    """The batched workload's size distribution (log-uniform in [2^8, 2^20], u32) at 256 arrays."""
+    from paper_2302_03317_gb300.inputs import batched_sizes
+    sizes = [int(v) for v in batched_sizes(256, seed=4)]
+    arrays = [np.arange(n, dtype=np.uint32) for n in sizes]
+    ts = [_to_dev(a) for a in arrays]
+    rip.shuffle_batched_(ts, 1000, check=True)
+    for i, (t, a) in enumerate(zip(ts, arrays)):
+        assert np.array_equal(_from_dev(t, a), oracle.shuffle(a, 1000 + i, _default_oplan(a.shape[0], 4))), i
