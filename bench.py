@@ -187,12 +187,18 @@ def run_batched(args, rip, torch, dist, ws, rank, local, barrier):
     total = sum(sizes)
     stream = torch.cuda.current_stream()
 
+    from paper_2302_03317_gb300 import tuner
+    table_path = tuner.default_table_path(4)
+    plans = None  # default plan of every array's own size
+    if args.plans == "tuned" and os.path.exists(table_path):
+        plans = tuner.plans_for(sizes, tuner.load_table(table_path))
+
     def batched(seed):
-        rip.shuffle_batched_(views, seed)
+        rip.shuffle_batched_(views, seed, plan=plans)
 
     def plain(seed):
         for i, v in enumerate(views):
-            rip.shuffle_(v, seed + i)
+            rip.shuffle_(v, seed + i, plan=plans[i] if plans else None)
 
     for i in range(args.warmup):
         batched(SEED + i)
@@ -238,7 +244,8 @@ def run_batched(args, rip, torch, dist, ws, rank, local, barrier):
             "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": f"batched: {args.arrays} u32 iota arrays, sizes log-uniform in [2^8, 2^20] "
-                                   f"(numpy default_rng({SEED})), seed base_seed + i, default plan per array",
+                                   f"(numpy default_rng({SEED})), seed base_seed + i, "
+                                   + ("tuned plan per size class" if plans else "default plan per array"),
                        "arrays": args.arrays, "elements": total, "elem_bytes": 4,
                        "l2": f"{total * 4 / 2**30:.1f} GiB of arrays vs 129 MB L2",
                        "parallelism": f"replicas{ws}" if ws > 1 else "single"},
@@ -273,6 +280,8 @@ def main():
                     help="capacity-*: 2^34 elements (64 / 128 GiB) with rip_capacity_plan (k = 1024, two levels); "
                          "batched: 4096 u32 arrays, sizes log-uniform in [2^8, 2^20], one batched call vs one call per array")
     ap.add_argument("--arrays", type=int, default=4096)
+    ap.add_argument("--plans", choices=["tuned", "default"], default="tuned",
+                    help="batched: per-size-class plans from the tuner's table (if present) or default plans")
     ap.add_argument("--ks", type=str, default="", help="profiling: comma list of k per level (overrides the default plan)")
     ap.add_argument("--Bs", type=str, default="", help="profiling: comma list of B per level")
     ap.add_argument("--Ts", type=str, default="", help="profiling: comma list of T per level")

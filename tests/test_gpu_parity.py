@@ -239,3 +239,22 @@ def test_batched_log_uniform_sizes():
     rip.shuffle_batched_(ts, 1000, check=True)
     for i, (t, a) in enumerate(zip(ts, arrays)):
         assert np.array_equal(_from_dev(t, a), oracle.shuffle(a, 1000 + i, _default_oplan(a.shape[0], 4))), i
+
+
+def test_batched_with_tuned_plans_replays_in_the_oracle():
+    """Per-size-class plans from the tuner's table: every array equals the oracle run with the
+    plan of its class (two arrays per class, 2^8 .. 2^20)."""
+    from paper_2302_03317_gb300 import tuner
+    import os
+    path = tuner.default_table_path(4)
+    if not os.path.exists(path):
+        pytest.skip("no tuned table")
+    table = tuner.load_table(path)
+    rng = np.random.default_rng(5)
+    sizes = [int((1 << c) * 2.0 ** rng.random()) for c in range(8, 21) for _ in range(2)]
+    plans = tuner.plans_for(sizes, table)
+    arrays = [np.arange(n, dtype=np.uint32) for n in sizes]
+    ts = [_to_dev(a) for a in arrays]
+    rip.shuffle_batched_(ts, 77, plan=plans, check=True)
+    for i, (t, a, p) in enumerate(zip(ts, arrays, plans)):
+        assert np.array_equal(_from_dev(t, a), oracle.shuffle(a, 77 + i, _oplan(p))), i
