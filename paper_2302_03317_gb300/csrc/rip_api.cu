@@ -413,6 +413,8 @@ bool capacity_plan_impl(uint64_t n, uint32_t w, rip_plan* p, uint32_t num_sms) {
     return true;
 }
 
+constexpr uint32_t kAuxStreams = 8;  // plan groups of one batched call run concurrently on these
+
 struct DevState {
     void* ws = nullptr;
     size_t ws_bytes = 0;
@@ -420,6 +422,8 @@ struct DevState {
     Status* status = nullptr;
     unsigned long long* digest_buf = nullptr;
     uint64_t last_info[3] = {0, 0, 0};
+    cudaStream_t aux[kAuxStreams] = {};
+    cudaEvent_t fork = nullptr, join[kAuxStreams] = {};
 };
 
 std::mutex g_mutex;
@@ -462,26 +466,8 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
     if (!any) return RIP_OK;
 
     const Layout lay = make_layout(ns, w, plan);
-    char* wsp = static_cast<char*>(ws);
-    if (wsp) {
-        if (ws_bytes < lay.total || (reinterpret_cast<uintptr_t>(wsp) & 255)) return RIP_EWORKSPACE;
-    } else {
-        std::lock_guard<std::mutex> lock(g_mutex);
-        if (ds->ws_bytes < lay.total) {
-            if (ds->ws) {
-                cudaDeviceSynchronize();
-                cudaFree(ds->ws);
-                ds->ws = nullptr;
-                ds->ws_bytes = 0;
-            }
-            if (cudaMalloc(&ds->ws, lay.total) != cudaSuccess) {
-                cudaGetLastError();
-                return RIP_ENOMEM;
-            }
-            ds->ws_bytes = lay.total;
-        }
-        wsp = static_cast<char*>(ds->ws);
-    }
+    char* wsp = static_cast<char*>(ws);  // resolved by the caller (run_groups)
+    if (!wsp || ws_bytes < lay.total || (reinterpret_cast<uintptr_t>(wsp) & 255)) return RIP_EWORKSPACE;
     ds->last_info[0] = std::max<uint64_t>(ds->last_info[0], lay.aux_bytes);
 
     const DevPlan dplan = to_dev(plan);
@@ -660,15 +646,48 @@ std::vector<Group> group_arrays(const uint64_t* ns, uint32_t count, uint32_t w, 
     return groups;
 }
 
-size_t groups_workspace(const std::vector<Group>& groups, const uint64_t* ns, uint32_t w) {
+// Workspace offsets of the groups (several groups run at once, each on its own slice);
+// returns the total, 0 for an invalid plan.
+size_t groups_workspace(const std::vector<Group>& groups, const uint64_t* ns, uint32_t w,
+                        std::vector<size_t>* offsets = nullptr) {
     size_t need = 0;
     for (const Group& g : groups) {
         if (validate_plan(g.plan, w) != RIP_OK) return 0;
         std::vector<uint64_t> v;
         for (uint32_t i : g.idx) v.push_back(ns[i]);
-        need = std::max(need, make_layout(v, w, g.plan).total);
+        if (offsets) offsets->push_back(need);
+        need += align_up(make_layout(v, w, g.plan).total, 256);
     }
     return need;
+}
+
+// The library-managed workspace of the current device, grown to `need` bytes.
+char* managed_workspace(DevState* ds, size_t need) {
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (ds->ws_bytes < need) {
+        if (ds->ws) {
+            cudaDeviceSynchronize();
+            cudaFree(ds->ws);
+            ds->ws = nullptr;
+            ds->ws_bytes = 0;
+        }
+        if (cudaMalloc(&ds->ws, need) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        ds->ws_bytes = need;
+    }
+    return static_cast<char*>(ds->ws);
+}
+
+bool aux_streams(DevState* ds) {
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (ds->fork) return true;
+    for (uint32_t i = 0; i < kAuxStreams; ++i) {
+        if (cudaStreamCreateWithFlags(&ds->aux[i], cudaStreamNonBlocking) != cudaSuccess) return false;
+        if (cudaEventCreateWithFlags(&ds->join[i], cudaEventDisableTiming) != cudaSuccess) return false;
+    }
+    return cudaEventCreateWithFlags(&ds->fork, cudaEventDisableTiming) == cudaSuccess;
 }
 
 int run_groups(void* const* ptrs, const uint64_t* ns, uint32_t count, uint32_t w, uint64_t base_seed,
@@ -689,7 +708,27 @@ int run_groups(void* const* ptrs, const uint64_t* ns, uint32_t count, uint32_t w
     const std::vector<Group> groups = group_arrays(ns, count, w, uniform, plans, ds->num_sms);
     for (const Group& g : groups)
         if (validate_plan(g.plan, w) != RIP_OK) return RIP_EINVAL;
-    for (const Group& g : groups) {  // consecutive runs on one stream reuse the workspace
+    std::vector<size_t> offs;
+    const size_t need = groups_workspace(groups, ns, w, &offs);
+    char* wsp = static_cast<char*>(ws);
+    if (wsp) {
+        if (ws_bytes < need || (reinterpret_cast<uintptr_t>(wsp) & 255)) return RIP_EWORKSPACE;
+    } else {
+        wsp = managed_workspace(ds, need);
+        if (!wsp) return RIP_ENOMEM;
+    }
+    // one group runs on the caller's stream; several run concurrently, group g on auxiliary
+    // stream g mod 8 with its own workspace slice, forked from and joined into the stream
+    const bool fan = groups.size() > 1;
+    if (fan) {
+        if (!aux_streams(ds)) return RIP_ECUDA;
+        if (cudaEventRecord(ds->fork, stream) != cudaSuccess) return RIP_ECUDA;
+        for (uint32_t a = 0; a < kAuxStreams && a < groups.size(); ++a)
+            if (cudaStreamWaitEvent(ds->aux[a], ds->fork, 0) != cudaSuccess) return RIP_ECUDA;
+    }
+    int rc = RIP_OK;
+    for (size_t gi = 0; gi < groups.size() && rc == RIP_OK; ++gi) {
+        const Group& g = groups[gi];
         std::vector<char*> p;
         std::vector<uint64_t> n, seeds;
         for (uint32_t i : g.idx) {
@@ -697,10 +736,16 @@ int run_groups(void* const* ptrs, const uint64_t* ns, uint32_t count, uint32_t w
             n.push_back(ns[i]);
             seeds.push_back(base_seed + i);
         }
-        const int rc = run_shuffle(p, n, seeds, w, g.plan, ws, ws_bytes, stream);
-        if (rc) return rc;
+        const cudaStream_t st = fan ? ds->aux[gi % kAuxStreams] : stream;
+        rc = run_shuffle(p, n, seeds, w, g.plan, wsp + offs[gi], need - offs[gi], st);
     }
-    return RIP_OK;
+    if (fan) {  // join even after an error, so the caller's stream orders everything enqueued
+        for (uint32_t a = 0; a < kAuxStreams && a < groups.size(); ++a) {
+            if (cudaEventRecord(ds->join[a], ds->aux[a]) != cudaSuccess) return RIP_ECUDA;
+            if (cudaStreamWaitEvent(stream, ds->join[a], 0) != cudaSuccess) return RIP_ECUDA;
+        }
+    }
+    return rc;
 }
 
 }  // namespace
