@@ -138,6 +138,17 @@ int rip_shuffle_batched_plans(void *const *ptrs, const uint64_t *ns, uint32_t co
                               uint64_t base_seed, const rip_plan *plans, void *ws, size_t ws_bytes,
                               rip_stream_t stream);
 
+/* Batched form with one seed per array (seeds: HOST array of `count` seeds; array i
+ * is shuffled with seeds[i]) and optionally one plan per array (plans NULL: every
+ * array its own default plan) -- for callers that batch independent requests, each
+ * of which keeps its own seed, e.g. a serving loop.  Otherwise as
+ * rip_shuffle_batched; the workspace size depends on ns and plans only. */
+size_t rip_shuffle_batched_ex_workspace_size(const uint64_t *ns, uint32_t count, uint32_t elem_bytes,
+                                             const rip_plan *plans);
+int rip_shuffle_batched_ex(void *const *ptrs, const uint64_t *ns, const uint64_t *seeds, uint32_t count,
+                           uint32_t elem_bytes, const rip_plan *plans, void *ws, size_t ws_bytes,
+                           rip_stream_t stream);
+
 /* Position-dependent 64-bit digest of data[0..n), computed on the device:
  *   H = sum_p splitmix64(p * 0x9E3779B97F4A7C15 ^ v(p)) mod 2^64,
  * v(p) = splitmix64 chained over the element's 8-byte little-endian words.

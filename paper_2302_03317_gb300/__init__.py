@@ -107,6 +107,11 @@ def _load():
         lib.rip_shuffle_batched_plans.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(u64), u32, u32, u64, pplan,
                                                   vp, sz, vp]
         lib.rip_shuffle_batched_plans.restype = i32
+        lib.rip_shuffle_batched_ex_workspace_size.argtypes = [ctypes.POINTER(u64), u32, u32, pplan]
+        lib.rip_shuffle_batched_ex_workspace_size.restype = sz
+        lib.rip_shuffle_batched_ex.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(u64), ctypes.POINTER(u64), u32, u32,
+                                               pplan, vp, sz, vp]
+        lib.rip_shuffle_batched_ex.restype = i32
         lib.rip_digest.argtypes = [vp, u64, u32, ctypes.POINTER(u64), vp]
         lib.rip_digest.restype = i32
         lib.rip_get_device_status.argtypes = [vp]
@@ -210,6 +215,22 @@ def rip_shuffle_batched_plans(ptrs: Sequence[int], ns: Sequence[int], elem_bytes
     narr = (ctypes.c_uint64 * count)(*ns)
     _check(_load().rip_shuffle_batched_plans(parr, narr, count, elem_bytes, base_seed, _plan_array(plans),
                                              ws_ptr or None, ws_bytes, stream), "rip_shuffle_batched_plans")
+
+
+def rip_shuffle_batched_ex_workspace_size(ns: Sequence[int], elem_bytes: int, plans=None) -> int:
+    arr = (ctypes.c_uint64 * len(ns))(*ns)
+    return int(_load().rip_shuffle_batched_ex_workspace_size(arr, len(ns), elem_bytes,
+                                                             _plan_array(plans) if plans else None))
+
+
+def rip_shuffle_batched_ex(ptrs: Sequence[int], ns: Sequence[int], seeds: Sequence[int], elem_bytes: int,
+                           plans=None, ws_ptr: int = 0, ws_bytes: int = 0, stream: int = 0) -> None:
+    count = len(ptrs)
+    parr = (ctypes.c_void_p * count)(*ptrs)
+    narr = (ctypes.c_uint64 * count)(*ns)
+    sarr = (ctypes.c_uint64 * count)(*[int(x) & 0xFFFFFFFFFFFFFFFF for x in seeds])
+    _check(_load().rip_shuffle_batched_ex(parr, narr, sarr, count, elem_bytes, _plan_array(plans) if plans else None,
+                                          ws_ptr or None, ws_bytes, stream), "rip_shuffle_batched_ex")
 
 
 def rip_digest(data_ptr: int, n: int, elem_bytes: int, stream: int = 0) -> int:

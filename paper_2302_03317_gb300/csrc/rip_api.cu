@@ -691,7 +691,8 @@ bool aux_streams(DevState* ds) {
 }
 
 int run_groups(void* const* ptrs, const uint64_t* ns, uint32_t count, uint32_t w, uint64_t base_seed,
-               const rip_plan* uniform, const rip_plan* plans, void* ws, size_t ws_bytes, cudaStream_t stream) {
+               const rip_plan* uniform, const rip_plan* plans, void* ws, size_t ws_bytes, cudaStream_t stream,
+               const uint64_t* seeds_arg = nullptr) {
     if (!valid_w(w)) return RIP_EINVAL;
     if (count && (!ptrs || !ns)) return RIP_EINVAL;
     for (uint32_t i = 0; i < count; ++i) {  // argument errors come before any device work
@@ -731,10 +732,11 @@ int run_groups(void* const* ptrs, const uint64_t* ns, uint32_t count, uint32_t w
         const Group& g = groups[gi];
         std::vector<char*> p;
         std::vector<uint64_t> n, seeds;
+        const uint64_t* seeds_in = seeds_arg;
         for (uint32_t i : g.idx) {
             p.push_back(static_cast<char*>(ptrs[i]));
             n.push_back(ns[i]);
-            seeds.push_back(base_seed + i);
+            seeds.push_back(seeds_in ? seeds_in[i] : base_seed + i);
         }
         const cudaStream_t st = fan ? ds->aux[gi % kAuxStreams] : stream;
         rc = run_shuffle(p, n, seeds, w, g.plan, wsp + offs[gi], need - offs[gi], st);
@@ -780,6 +782,14 @@ size_t rip_shuffle_batched_workspace_size(const uint64_t* ns, uint32_t count, ui
                             elem_bytes);
 }
 
+size_t rip_shuffle_batched_ex_workspace_size(const uint64_t* ns, uint32_t count, uint32_t elem_bytes,
+                                             const rip_plan* plans) {
+    if (!valid_w(elem_bytes) || (count && !ns)) return 0;
+    DevState* ds = dev_state(nullptr);
+    return groups_workspace(group_arrays(ns, count, elem_bytes, nullptr, plans, ds ? ds->num_sms : 152), ns,
+                            elem_bytes);
+}
+
 size_t rip_shuffle_batched_plans_workspace_size(const uint64_t* ns, uint32_t count, uint32_t elem_bytes,
                                                 const rip_plan* plans) {
     if (!valid_w(elem_bytes) || (count && (!ns || !plans))) return 0;
@@ -802,6 +812,14 @@ int rip_shuffle_batched(void* const* ptrs, const uint64_t* ns, uint32_t count, u
                         uint64_t base_seed, const rip_plan* plan, void* ws, size_t ws_bytes, rip_stream_t stream) {
     return run_groups(ptrs, ns, count, elem_bytes, base_seed, plan, nullptr, ws, ws_bytes,
                       reinterpret_cast<cudaStream_t>(stream));
+}
+
+int rip_shuffle_batched_ex(void* const* ptrs, const uint64_t* ns, const uint64_t* seeds, uint32_t count,
+                           uint32_t elem_bytes, const rip_plan* plans, void* ws, size_t ws_bytes,
+                           rip_stream_t stream) {
+    if (count && !seeds) return RIP_EINVAL;
+    return run_groups(ptrs, ns, count, elem_bytes, 0, nullptr, plans, ws, ws_bytes,
+                      reinterpret_cast<cudaStream_t>(stream), seeds);
 }
 
 int rip_shuffle_batched_plans(void* const* ptrs, const uint64_t* ns, uint32_t count, uint32_t elem_bytes,
