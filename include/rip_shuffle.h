@@ -182,8 +182,9 @@ int rip_last_call_info(uint64_t out[3]);
  * every GPU that loads the library holds until the process exits; the call
  * performs no allocation.  Inputs whose workspace
  * (rip_shuffle_workspace_size) exceeds the array are rejected with
- * RIP_ETOOLARGE before anything is enqueued; with the default plan that is
- * about 2^22 elements of 4 or 8 bytes or 2^20 16-byte records.  The first call
+ * RIP_ETOOLARGE before anything is enqueued; with the default plans every
+ * power-of-two size up to 2^28 4-byte, 2^26 8-byte and 2^20 16-byte elements
+ * fits (the workspace is not monotone in n: ask rip_shuffle_workspace_size).  The first call
  * on a device looks up the array's device address (a one-time set-up); make
  * that first call before any stream capture.  All calls share the array and
  * each call clears what must start at zero; calls that overlap on the GPU race

@@ -376,11 +376,21 @@ bool default_plan_impl(uint64_t n, uint32_t w, rip_plan* p, uint32_t num_sms) {
     T0 = (T0 + B - 1) / B * B;
     T0 = std::min<uint64_t>(T0, (uint64_t)B << 20);
     T0 = T0 / B * B;
+    // level 1 and below: where the root's children run in place (above ~32K elements), k is
+    // chosen so that their children hold about 8K elements -- the on-SM solver then finishes
+    // them with one more scatter or none (measured on GB300: 1.4-2.3x faster from 2^22 to
+    // 2^28 elements than k = 256 at every level); smaller children keep the root's k
+    const uint64_t m1 = n / k;
+    uint32_t k1 = k;
+    if (m1 > 32768) {
+        k1 = 16;
+        while (k1 < 256 && (uint64_t)k1 * 8192 < m1) k1 *= 2;
+    }
     p->num_levels = 2;
     p->level[0].k = k;
     p->level[0].block = B;
     p->level[0].tile = T0;
-    p->level[1].k = k;
+    p->level[1].k = k1;
     p->level[1].block = B;
     p->level[1].tile = std::min<uint64_t>((uint64_t)B << 20, (uint64_t)1 << 40) / B * B;
     p->base = 4096;

@@ -46,12 +46,13 @@ def test_noalloc_equals_rip_shuffle_ex_on_two_calls(n, w, plan):
 
 def test_noalloc_rejects_inputs_beyond_its_workspace():
     lib = rip._load()
-    n, w = 1 << 25, 8
-    assert rip.rip_shuffle_workspace_size(n, w) > 32 << 20
-    x = torch.arange(n, dtype=torch.int64, device="cuda")
+    # the first of these whose default-plan workspace exceeds the fixed array
+    n, w = next((n, w) for n, w in [(1 << 21, 16), (1 << 27, 8), (1 << 29, 4)]
+                if rip.rip_shuffle_workspace_size(n, w) > 32 << 20)
+    x = torch.arange(n * w // 8, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
     rc = lib.rip_shuffle_noalloc(ctypes.c_void_p(x.data_ptr()), n, w, 3, None, ctypes.c_void_p(stream))
     assert rc == rip.RIP_ETOOLARGE
     assert "too large" in rip.rip_strerror(rc)
     torch.cuda.synchronize()
-    assert torch.equal(x, torch.arange(n, dtype=torch.int64, device="cuda"))  # untouched
+    assert torch.equal(x, torch.arange(n * w // 8, dtype=torch.int64, device="cuda"))  # untouched
