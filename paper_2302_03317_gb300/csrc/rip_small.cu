@@ -56,32 +56,6 @@ __device__ __forceinline__ bool lemire32(uint32_t x, uint32_t s, uint32_t& v) {
     return true;
 }
 
-// Fisher-Yates over Z[0..len) by the calling thread (Sec. 2.2): all partner
-// draws first (one Philox call per four positions, independent iterations),
-// stored in H[1..len), then the dependent swap chain.  len < 2^16.
-__device__ void fy_thread(uint16_t* Z, uint16_t* H, uint32_t len, PhiloxKey key, uint32_t L, uint64_t leaf_o) {
-    const uint64_t q_first = (leaf_o + 1) >> 2, q_last = (leaf_o + len - 1) >> 2;
-    for (uint64_t q = q_first; q <= q_last; ++q) {
-        const uint4 r = philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), L | (kTagFy << 8), (uint32_t)leaf_o, key);
-        const uint32_t w4[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-        for (uint32_t wd = 0; wd < 4; ++wd) {
-            const uint64_t i64 = 4 * q + wd - leaf_o;  // step index of this word
-            if (4 * q + wd < leaf_o + 1 || i64 >= len) continue;
-            const uint32_t i = (uint32_t)i64;
-            uint32_t v;
-            if (!lemire32(w4[wd], i + 1, v)) v = (uint32_t)fy_draw_retry(key, L, leaf_o, leaf_o + i, i + 1);
-            H[i] = (uint16_t)v;
-        }
-    }
-    for (uint32_t i = len - 1; i >= 1; --i) {
-        const uint32_t j = H[i];
-        const uint16_t zi = Z[i];
-        Z[i] = Z[j];
-        Z[j] = zi;
-    }
-}
-
 // Partner draws H[i] (i >= 1) of a leaf, computed by the whole block.
 __device__ void fy_draws(uint16_t* H, uint32_t len, PhiloxKey key, uint32_t L, uint64_t leaf_o) {
     for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
@@ -193,10 +167,67 @@ __device__ void fy_block(uint16_t* Z, uint16_t* draws, uint32_t len, PhiloxKey k
 
 // Children of a scattered range: leaves are finished right away, larger ones
 // are pushed for another scatter.  start(b) = first output index of bucket b.
+// Partner draws H[1..len) of a leaf by the calling thread (one Philox call per four positions).
+__device__ void fy_draws_thread(uint16_t* H, uint32_t len, PhiloxKey key, uint32_t L, uint64_t leaf_o) {
+    const uint64_t q_first = (leaf_o + 1) >> 2, q_last = (leaf_o + len - 1) >> 2;
+    for (uint64_t q = q_first; q <= q_last; ++q) {
+        const uint4 r = philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), L | (kTagFy << 8), (uint32_t)leaf_o, key);
+        const uint32_t w4[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (uint32_t wd = 0; wd < 4; ++wd) {
+            const uint64_t i64 = 4 * q + wd - leaf_o;  // step index of this word
+            if (4 * q + wd < leaf_o + 1 || i64 >= len) continue;
+            const uint32_t i = (uint32_t)i64;
+            uint32_t v;
+            if (!lemire32(w4[wd], i + 1, v)) v = (uint32_t)fy_draw_retry(key, L, leaf_o, leaf_o + i, i + 1);
+            H[i] = (uint16_t)v;
+        }
+    }
+}
+
+// Leaves at least this large get their draws from a whole warp; smaller ones from their thread.
+constexpr uint32_t kWarpDrawsMin = 128;
+
+// Partner draws of one leaf child, by the lanes of one warp (one Philox call per lane and
+// group of four positions); stored in H[1..len).
+__device__ __forceinline__ void fy_draws_warp(uint16_t* H, uint32_t len, PhiloxKey key, uint32_t L, uint64_t leaf_o) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t q_first = (leaf_o + 1) >> 2, q_last = (leaf_o + len - 1) >> 2;
+    for (uint64_t q = q_first + lane; q <= q_last; q += 32u) {
+        const uint4 r = philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), L | (kTagFy << 8), (uint32_t)leaf_o, key);
+        const uint32_t w4[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (uint32_t wd = 0; wd < 4; ++wd) {
+            const uint64_t i64 = 4 * q + wd - leaf_o;  // step index of this word
+            if (4 * q + wd < leaf_o + 1 || i64 >= len) continue;
+            const uint32_t i = (uint32_t)i64;
+            uint32_t v;
+            if (!lemire32(w4[wd], i + 1, v)) v = (uint32_t)fy_draw_retry(key, L, leaf_o, leaf_o + i, i + 1);
+            H[i] = (uint16_t)v;
+        }
+    }
+}
+
 template <typename StartFn>
 __device__ void finish_children(SmallShared& sh, uint16_t* P0, uint16_t* X, uint16_t* Y, uint32_t a, uint32_t len,
                                 uint32_t k, uint32_t L, uint32_t buf, const DevPlan& plan, PhiloxKey key,
                                 uint64_t o_r, Status* status, StartFn start) {
+    // leaf children: partner draws of the large ones first, one warp per child (the scatter's
+    // source range is free now and holds them), then one thread per child draws for a small one
+    // and runs the child's swap chain
+    const uint32_t warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const bool warp_draws = len >= 96u * k;  // children of about 96 or more elements expected
+    if (warp_draws) {
+        for (uint32_t b = warp; b < k; b += nwarps) {
+            const uint32_t sb = start(b);
+            const uint32_t se = b + 1 < k ? start(b + 1) : len;
+            if (se > len || sb >= se) continue;
+            const uint32_t size = se - sb;
+            if (size >= kWarpDrawsMin && plan.is_leaf(size, L + 1))
+                fy_draws_warp(X + a + sb, size, key, L + 1, o_r + sb);
+        }
+        __syncthreads();
+    }
     for (uint32_t b = threadIdx.x; b < k; b += blockDim.x) {
         const uint32_t sb = start(b);
         const uint32_t se = b + 1 < k ? start(b + 1) : len;
@@ -208,8 +239,16 @@ __device__ void finish_children(SmallShared& sh, uint16_t* P0, uint16_t* X, uint
         }
         if (size == 1 || plan.is_leaf(size, L + 1)) {
             uint16_t* Z = Y + a + sb;
-            // the scatter's source range is free now: it holds the child's draws
-            if (size > 1) fy_thread(Z, X + a + sb, size, key, L + 1, o_r + sb);
+            if (size > 1) {
+                uint16_t* H = X + a + sb;
+                if (size < kWarpDrawsMin || !warp_draws) fy_draws_thread(H, size, key, L + 1, o_r + sb);
+                for (uint32_t i = size - 1; i >= 1; --i) {
+                    const uint32_t j = H[i];
+                    const uint16_t zi = Z[i];
+                    Z[i] = Z[j];
+                    Z[j] = zi;
+                }
+            }
             if (Y != P0)
                 for (uint32_t j = 0; j < size; ++j) P0[a + sb + j] = Z[j];
         } else {
