@@ -271,7 +271,7 @@ __global__ void resolve_kernel(LevelArgs a) {
 // ------------------------------------------------------------------ permute
 
 template <typename U>
-__global__ void __launch_bounds__(kPermuteThreads) permute_kernel(LevelArgs a, uint32_t w) {
+__global__ void __launch_bounds__(kPermuteThreads, 4) permute_kernel(LevelArgs a, uint32_t w) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t units = a.B * w / (uint32_t)sizeof(U);
     const uint32_t tid = threadIdx.x;
