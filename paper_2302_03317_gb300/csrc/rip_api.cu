@@ -115,7 +115,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 uint32_t small_max_m_for(uint32_t w) {
     const size_t fixed = small_fixed_smem();
-    const size_t m = (kSmemOptin - fixed) / (4 + w);
+    const size_t m = (kSmemOptin - fixed - 16) / (4 + w);  // 16: alignment slack of D
     return (uint32_t)std::min<size_t>(m & ~size_t(7), kMediumMaxM);
 }
 

@@ -7,8 +7,13 @@
 // canonical (unrotated) order with one coalesced pass.  HBM traffic: one read
 // and one write of the subproblem, whatever the number of levels inside.
 //
-// Shared memory: [fixed scratch | P0 (2m) | P1 (2m) | D (w*m)].  In "medium"
-// mode D lives in a per-CTA slice of global scratch instead (m up to 48K).
+// Shared memory: [fixed scratch | P0 (2m) | P1 (2m) | D (w*m + 16)].  D is
+// filled by bulk (TMA) copies issued when the subproblem starts and completing
+// on an mbarrier, so the load overlaps the whole index computation (which needs
+// no data); D is shifted by up to 15 bytes so that the copy of the larger
+// rotation piece starts 16-byte aligned on both sides, and the ragged rest is
+// copied by the threads.  In "medium" mode D lives in a per-CTA slice of global
+// scratch instead (m up to 48K) and is loaded by the threads.
 #include "rip_internal.cuh"
 
 namespace rip {
@@ -26,7 +31,7 @@ struct GeneralScratch {         // scatter of a range with several tiles or k > 
     uint32_t tbl[kSmallTbl / 2]; // per (ranking warp, bucket): running count in a round
 };
 struct FastScratch {               // single-tile scatter with k <= 256
-    uint32_t hist[kWarps * 128];   // per (warp, bucket pair): two 16-bit counts, then first output indices
+    uint16_t hist[kWarps * 256];   // per (warp, bucket): count, then the warp's next output index
     uint32_t start[256];           // per bucket: total, then first output index of the bucket
     uint32_t mask[kWarps * 64];    // per (warp, low 6 bucket bits): lanes of the current step
 };
@@ -38,6 +43,7 @@ struct SmallShared {
     };
     uint64_t stack[kSmallStack]; // pending scatter ranges
     uint32_t scan[32];
+    uint64_t load_bar;           // bulk copy of the subproblem's data into D
     uint32_t stack_top;
     uint32_t cur_hi, cur_lo;
     uint32_t flag;
@@ -165,69 +171,56 @@ __device__ void fy_block(uint16_t* Z, uint16_t* draws, uint32_t len, PhiloxKey k
     __syncthreads();
 }
 
+// The four partner draws of the Philox call with counter q (positions 4q .. 4q+3) that fall in
+// steps [1, len) of the leaf starting at global position leaf_o; stored in H[step].
+__device__ __forceinline__ void fy_store_group(uint16_t* H, uint4 r, uint64_t q, uint32_t len, PhiloxKey key,
+                                               uint32_t L, uint64_t leaf_o) {
+    const uint32_t w4[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (uint32_t wd = 0; wd < 4; ++wd) {
+        const uint64_t i64 = 4 * q + wd - leaf_o;  // step index of this word
+        if (4 * q + wd < leaf_o + 1 || i64 >= len) continue;
+        const uint32_t i = (uint32_t)i64;
+        uint32_t v;
+        if (!lemire32(w4[wd], i + 1, v)) v = (uint32_t)fy_draw_retry(key, L, leaf_o, leaf_o + i, i + 1);
+        H[i] = (uint16_t)v;
+    }
+}
+
+// Partner draws of one leaf child, by `step` threads together: the calling thread takes the
+// groups of four positions sub, sub + step, ...; two Philox calls are in flight at a time.
+__device__ __forceinline__ void fy_draws_part(uint16_t* H, uint32_t len, PhiloxKey key, uint32_t L, uint64_t leaf_o,
+                                              uint32_t sub, uint32_t step) {
+    const uint64_t q_first = (leaf_o + 1) >> 2, q_last = (leaf_o + len - 1) >> 2;
+    const uint32_t tag = L | (kTagFy << 8), o32 = (uint32_t)leaf_o;
+    for (uint64_t q = q_first + sub; q <= q_last; q += 2u * step) {
+        const uint64_t q2 = q + step;  // may lie past the leaf: computed, not stored
+        const uint4 r = philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), tag, o32, key);
+        const uint4 r2 = philox4x32_10((uint32_t)q2, (uint32_t)(q2 >> 32), tag, o32, key);
+        fy_store_group(H, r, q, len, key, L, leaf_o);
+        if (q2 <= q_last) fy_store_group(H, r2, q2, len, key, L, leaf_o);
+    }
+}
+
 // Children of a scattered range: leaves are finished right away, larger ones
 // are pushed for another scatter.  start(b) = first output index of bucket b.
-// Partner draws H[1..len) of a leaf by the calling thread (one Philox call per four positions).
-__device__ void fy_draws_thread(uint16_t* H, uint32_t len, PhiloxKey key, uint32_t L, uint64_t leaf_o) {
-    const uint64_t q_first = (leaf_o + 1) >> 2, q_last = (leaf_o + len - 1) >> 2;
-    for (uint64_t q = q_first; q <= q_last; ++q) {
-        const uint4 r = philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), L | (kTagFy << 8), (uint32_t)leaf_o, key);
-        const uint32_t w4[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-        for (uint32_t wd = 0; wd < 4; ++wd) {
-            const uint64_t i64 = 4 * q + wd - leaf_o;  // step index of this word
-            if (4 * q + wd < leaf_o + 1 || i64 >= len) continue;
-            const uint32_t i = (uint32_t)i64;
-            uint32_t v;
-            if (!lemire32(w4[wd], i + 1, v)) v = (uint32_t)fy_draw_retry(key, L, leaf_o, leaf_o + i, i + 1);
-            H[i] = (uint16_t)v;
-        }
-    }
-}
-
-// Leaves at least this large get their draws from a whole warp; smaller ones from their thread.
-constexpr uint32_t kWarpDrawsMin = 128;
-
-// Partner draws of one leaf child, by the lanes of one warp (one Philox call per lane and
-// group of four positions); stored in H[1..len).
-__device__ __forceinline__ void fy_draws_warp(uint16_t* H, uint32_t len, PhiloxKey key, uint32_t L, uint64_t leaf_o) {
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint64_t q_first = (leaf_o + 1) >> 2, q_last = (leaf_o + len - 1) >> 2;
-    for (uint64_t q = q_first + lane; q <= q_last; q += 32u) {
-        const uint4 r = philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), L | (kTagFy << 8), (uint32_t)leaf_o, key);
-        const uint32_t w4[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-        for (uint32_t wd = 0; wd < 4; ++wd) {
-            const uint64_t i64 = 4 * q + wd - leaf_o;  // step index of this word
-            if (4 * q + wd < leaf_o + 1 || i64 >= len) continue;
-            const uint32_t i = (uint32_t)i64;
-            uint32_t v;
-            if (!lemire32(w4[wd], i + 1, v)) v = (uint32_t)fy_draw_retry(key, L, leaf_o, leaf_o + i, i + 1);
-            H[i] = (uint16_t)v;
-        }
-    }
-}
-
 template <typename StartFn>
 __device__ void finish_children(SmallShared& sh, uint16_t* P0, uint16_t* X, uint16_t* Y, uint32_t a, uint32_t len,
                                 uint32_t k, uint32_t L, uint32_t buf, const DevPlan& plan, PhiloxKey key,
                                 uint64_t o_r, Status* status, StartFn start) {
-    // leaf children: partner draws of the large ones first, one warp per child (the scatter's
-    // source range is free now and holds them), then one thread per child draws for a small one
-    // and runs the child's swap chain
-    const uint32_t warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const bool warp_draws = len >= 96u * k;  // children of about 96 or more elements expected
-    if (warp_draws) {
-        for (uint32_t b = warp; b < k; b += nwarps) {
-            const uint32_t sb = start(b);
-            const uint32_t se = b + 1 < k ? start(b + 1) : len;
-            if (se > len || sb >= se) continue;
-            const uint32_t size = se - sb;
-            if (size >= kWarpDrawsMin && plan.is_leaf(size, L + 1))
-                fy_draws_warp(X + a + sb, size, key, L + 1, o_r + sb);
-        }
-        __syncthreads();
+    // leaf children: partner draws first, by every thread (blockDim/k threads per child; the
+    // scatter's source range is free now and holds them), then one thread per child runs the
+    // child's swap chain
+    const uint32_t tpc = k >= blockDim.x ? 1u : blockDim.x / k;  // both powers of two
+    for (uint32_t b = threadIdx.x / tpc; b < k; b += blockDim.x / tpc) {
+        const uint32_t sb = start(b);
+        const uint32_t se = b + 1 < k ? start(b + 1) : len;
+        if (se > len || sb >= se) continue;
+        const uint32_t size = se - sb;
+        if (size > 1 && plan.is_leaf(size, L + 1))
+            fy_draws_part(X + a + sb, size, key, L + 1, o_r + sb, threadIdx.x % tpc, tpc);
     }
+    __syncthreads();
     for (uint32_t b = threadIdx.x; b < k; b += blockDim.x) {
         const uint32_t sb = start(b);
         const uint32_t se = b + 1 < k ? start(b + 1) : len;
@@ -239,9 +232,23 @@ __device__ void finish_children(SmallShared& sh, uint16_t* P0, uint16_t* X, uint
         }
         if (size == 1 || plan.is_leaf(size, L + 1)) {
             uint16_t* Z = Y + a + sb;
-            if (size > 1) {
-                uint16_t* H = X + a + sb;
-                if (size < kWarpDrawsMin || !warp_draws) fy_draws_thread(H, size, key, L + 1, o_r + sb);
+            const uint16_t* H = X + a + sb;
+            if (Y != P0) {
+                // the swap chain writes each final position straight to P0: step i fixes
+                // position i (later steps touch only positions below i), so only Z[j] is
+                // written back; out may coincide with H, whose entry i is read before
+                uint16_t* out = P0 + a + sb;
+                uint32_t j = size > 1 ? H[size - 1] : 0u;
+                for (uint32_t i = size - 1; i >= 1; --i) {
+                    const uint32_t jn = i > 1 ? H[i - 1] : 0u;  // entry i-1 is not written at step i
+                    const uint16_t zj = Z[j];
+                    const uint16_t zi = Z[i];
+                    out[i] = zj;
+                    Z[j] = zi;
+                    j = jn;
+                }
+                out[0] = Z[0];
+            } else {
                 for (uint32_t i = size - 1; i >= 1; --i) {
                     const uint32_t j = H[i];
                     const uint16_t zi = Z[i];
@@ -249,8 +256,6 @@ __device__ void finish_children(SmallShared& sh, uint16_t* P0, uint16_t* X, uint
                     Z[j] = zi;
                 }
             }
-            if (Y != P0)
-                for (uint32_t j = 0; j < size; ++j) P0[a + sb + j] = Z[j];
         } else {
             const uint32_t slot = atomicAdd(&sh.stack_top, 1u);
             if (slot < kSmallStack)
@@ -268,8 +273,11 @@ __device__ void finish_children(SmallShared& sh, uint16_t* P0, uint16_t* X, uint
 // the four buckets of one Philox call per group (kept packed in registers) and
 // counts them in the warp's histogram row.  Prefix: rows become the first
 // output index of (warp, bucket).  Pass 2: the warp walks its run in position
-// order, 32 positions per step; match_any gives the rank inside the step and
-// one shared atomic per bucket and step advances the warp's row.
+// order, 32 positions per step; the lanes of the step with the same bucket
+// (the rank inside the step) come from a shared-memory mask row indexed by the
+// low six bucket bits (one atomic OR per lane) and one ballot per higher bit
+// -- on GB300 a ballot costs more issue time than a shared atomic -- and the
+// lowest of them advances the warp's row (only the warp itself touches it).
 constexpr uint32_t kFastGroups = 24;  // groups per warp: 16 warps x 24 x 128 >= 48K + 3
 
 __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint32_t a, uint32_t len, uint32_t L,
@@ -277,7 +285,6 @@ __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, 
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t k = plan.k[plan.idx(L)];
     const uint32_t kbits = log2_pow2(k);
-    const uint32_t kh = (k + 1u) / 2u;  // packed histogram words per warp
     uint16_t* X = buf ? P1 : P0;
     uint16_t* Y = buf ? P0 : P1;
     const uint64_t o_r = sub_o + a;
@@ -286,8 +293,9 @@ __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, 
     const uint32_t ngroups = (len + delta + 127u) / 128u;
     const uint32_t gpw = (ngroups + kWarps - 1) / kWarps;  // groups per warp (<= kFastGroups)
     const uint32_t g0 = warp * gpw;
-    uint32_t* hist = sh.f.hist;
-    for (uint32_t j = tid; j < kWarps * kh; j += blockDim.x) hist[j] = 0;
+    uint16_t* hist = sh.f.hist;
+    uint32_t* hist32 = reinterpret_cast<uint32_t*>(hist);  // two 16-bit counters per word
+    for (uint32_t j = tid; j < kWarps * 128u; j += blockDim.x) hist32[j] = 0;
     for (uint32_t j = tid; j < kWarps * 64u; j += blockDim.x) sh.f.mask[j] = 0;
     __syncthreads();
 
@@ -305,24 +313,17 @@ __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, 
                 const uint32_t b = bucket_of(w4[j], k);
                 bk[g] |= b << (8 * j);
                 const uint32_t v = v0 + j;
-                if (v >= delta && v - delta < len) atomicAdd(&hist[warp * kh + (b >> 1)], 1u << (16u * (b & 1u)));
+                if (v >= delta && v - delta < len) atomicAdd(&hist32[warp * 128u + (b >> 1)], 1u << (16u * (b & 1u)));
             }
         }
     }
     __syncthreads();
     // rows -> first output index of (warp, bucket)
     for (uint32_t b = tid; b < k; b += blockDim.x) {
-        const uint32_t sh16 = 16u * (b & 1u);
         uint32_t acc = 0;
         for (uint32_t w = 0; w < kWarps; ++w) {
-            uint32_t* cell = &hist[w * kh + (b >> 1)];
-            const uint32_t c = (*cell >> sh16) & 0xFFFFu;
-            // each half-word belongs to one thread: move ours from c to acc without
-            // touching the other half (no borrow or carry crosses the halves)
-            if (acc >= c)
-                atomicAdd(cell, (acc - c) << sh16);
-            else
-                atomicSub(cell, (c - acc) << sh16);
+            const uint32_t c = hist[w * 256u + b];  // each 16-bit counter has one owner here
+            hist[w * 256u + b] = (uint16_t)acc;
             acc += c;
         }
         sh.f.start[b] = acc;  // bucket total
@@ -336,8 +337,12 @@ __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, 
         if (i1 < k) sh.f.start[i1] = ex + v0;
     }
     __syncthreads();
+    for (uint32_t j = tid; j < kWarps * 256u; j += blockDim.x)
+        if ((j & 255u) < k) hist[j] = (uint16_t)(hist[j] + sh.f.start[j & 255u]);
+    __syncthreads();
 
     const uint32_t lt_mask = (1u << lane) - 1u;
+    uint16_t* row = hist + warp * 256u;
     uint32_t* mrow = sh.f.mask + warp * 64u;
 #pragma unroll
     for (uint32_t g = 0; g < kFastGroups; ++g) {
@@ -349,9 +354,8 @@ __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, 
                 const uint32_t b = (packed >> (8u * (lane & 3u))) & 0xFFu;
                 const uint32_t v = vg + 32u * st + lane;
                 const bool valid = v >= delta && v - delta < len;
-                // lanes with the same bucket: low 6 bits through the warp's mask row, the rest by ballot
                 if (valid) atomicOr(&mrow[b & 63u], 1u << lane);
-                uint32_t peers = __ballot_sync(0xffffffffu, valid);
+                uint32_t peers = 0xffffffffu;
 #pragma unroll
                 for (uint32_t i = 6; i < 8; ++i) {
                     if (i < kbits) {
@@ -362,17 +366,15 @@ __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, 
                 }
                 __syncwarp();
                 peers &= valid ? mrow[b & 63u] : 0u;
-                const uint32_t leader = valid ? (uint32_t)(__ffs(peers) - 1) : lane;
-                uint32_t base = 0;
-                if (valid && lane == leader) {
-                    const uint32_t sh16 = 16u * (b & 1u);
-                    base = ((atomicAdd(&hist[warp * kh + (b >> 1)], (uint32_t)__popc(peers) << sh16) >> sh16) & 0xFFFFu)
-                           + sh.f.start[b];
+                // the step's lanes with this bucket read the row together; the lowest writes it
+                // back and clears the mask entry (a 16-bit store: the neighbour counter is untouched)
+                const uint32_t base = valid ? (uint32_t)row[b] : 0u;
+                __syncwarp();
+                if (valid && (peers & lt_mask) == 0) {
+                    row[b] = (uint16_t)(base + (uint32_t)__popc(peers));
+                    mrow[b & 63u] = 0u;
                 }
                 __syncwarp();
-                if (valid && lane == leader) mrow[b & 63u] = 0u;  // each bucket's leader clears its class
-                __syncwarp();
-                base = __shfl_sync(0xffffffffu, base, (int)leader);
                 if (valid) {
                     const uint32_t d = base + __popc(peers & lt_mask);
                     if (d < len) Y[a + d] = X[a + (v - delta)];
@@ -552,6 +554,12 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(SmallArgs args) {
     const uint32_t count = min(*args.count, args.capacity);
     const uint32_t tid = threadIdx.x;
     const DevPlan& plan = args.plan;
+    if (tid == 0) {
+        mbar_init(&sh.load_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t loads = 0;  // completed phases of load_bar
 
     for (uint32_t item = blockIdx.x; item < count; item += gridDim.x) {
         const Sub s = args.list[item];
@@ -561,36 +569,93 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(SmallArgs args) {
         const PhiloxKey key = make_key(ad.seed);
         uint16_t* P0 = reinterpret_cast<uint16_t*>(dyn);
         uint16_t* P1 = P0 + ((m + 7u) & ~7u);
-        T* D = args.medium ? reinterpret_cast<T*>(args.gscratch + (uint64_t)blockIdx.x * args.gslot_bytes)
-                           : reinterpret_cast<T*>(P1 + ((m + 7u) & ~7u));
-
-        // load through the rotation, eight independent loads in flight per thread
-        for (uint32_t i0 = tid; i0 < m; i0 += 8u * blockDim.x) {
-            T v[8];
+        T* D;
+        bool bulk = false;  // D arrives through load_bar
+        if (args.medium) {
+            // load through the rotation, eight independent loads in flight per thread
+            D = reinterpret_cast<T*>(args.gscratch + (uint64_t)blockIdx.x * args.gslot_bytes);
+            for (uint32_t i0 = tid; i0 < m; i0 += 8u * blockDim.x) {
+                T v[8];
 #pragma unroll
-            for (uint32_t j = 0; j < 8; ++j) {
-                const uint32_t i = i0 + j * blockDim.x;
-                if (i < m) v[j] = base[phys_index(s, i)];
-            }
+                for (uint32_t j = 0; j < 8; ++j) {
+                    const uint32_t i = i0 + j * blockDim.x;
+                    if (i < m) v[j] = base[phys_index(s, i)];
+                }
 #pragma unroll
-            for (uint32_t j = 0; j < 8; ++j) {
-                const uint32_t i = i0 + j * blockDim.x;
-                if (i < m) {
-                    D[i] = v[j];
-                    P0[i] = (uint16_t)i;
+                for (uint32_t j = 0; j < 8; ++j) {
+                    const uint32_t i = i0 + j * blockDim.x;
+                    if (i < m) D[i] = v[j];
                 }
             }
+        } else {
+            // the rotation's pieces: logical [0, nA) from physical o+eps.., [nA, m) from o..; each
+            // piece's 16-byte-aligned middle goes by bulk copy when its shared-memory start is
+            // aligned too (the larger piece fixes D's shift), the rest by the threads
+            const uint32_t q = W >= 16 ? 1u : 16u / W;  // elements per 16 bytes
+            const uint32_t nA = m - s.eps;
+            const uintptr_t gA = reinterpret_cast<uintptr_t>(base + s.o + s.eps);
+            const uintptr_t gB = reinterpret_cast<uintptr_t>(base + s.o);
+            auto first_aligned = [&](uint32_t L0, uint32_t L1, uintptr_t g) -> uint32_t {
+                return min(L1, L0 + (uint32_t)(((16u - (g & 15u)) & 15u) / W));
+            };
+            const uint32_t fa = first_aligned(0u, nA, gA), fb = first_aligned(nA, m, gB);
+            const uint32_t dshift = nA >= s.eps ? (q - fa % q) % q : (q - fb % q) % q;
+            D = reinterpret_cast<T*>(P1 + ((m + 7u) & ~7u)) + dshift;
+            auto bulk_range = [&](uint32_t L0, uint32_t L1, uintptr_t g, uint32_t f, uint32_t& lo, uint32_t& hi) {
+                lo = hi = L0;
+                const uint32_t e = f + (L1 - f) / q * q;
+                if (e > f && ((g + (uintptr_t)(f - L0) * W) & 15u) == 0 && (dshift + f) % q == 0) {
+                    lo = f;
+                    hi = e;
+                }
+            };
+            uint32_t aLo, aHi, bLo, bHi;
+            bulk_range(0u, nA, gA, fa, aLo, aHi);
+            bulk_range(nA, m, gB, fb, bLo, bHi);
+            if (bLo == bHi) bLo = bHi = m;
+            if (tid == 0) {
+                const uint32_t bytes = (aHi - aLo + bHi - bLo) * (uint32_t)W;
+                if (bytes) {
+                    mbar_arrive_expect_tx(&sh.load_bar, bytes);
+                    auto issue = [&](uint32_t lo, uint32_t hi, uintptr_t g, uint32_t L0) {
+                        const char* src = reinterpret_cast<const char*>(g + (uintptr_t)(lo - L0) * W);
+                        char* dst = reinterpret_cast<char*>(D + lo);
+                        const uint32_t nbytes = (hi - lo) * (uint32_t)W;
+                        for (uint32_t off = 0; off < nbytes; off += 32768u)
+                            bulk_g2s(dst + off, src + off, min(32768u, nbytes - off), &sh.load_bar);
+                    };
+                    if (aHi > aLo) issue(aLo, aHi, gA, 0u);
+                    if (bHi > bLo) issue(bLo, bHi, gB, nA);
+                } else {
+                    mbar_arrive(&sh.load_bar);
+                }
+            }
+            for (uint32_t i = tid; i < aLo; i += blockDim.x) D[i] = base[phys_index(s, i)];
+            for (uint32_t i = aHi + tid; i < bLo; i += blockDim.x) D[i] = base[phys_index(s, i)];
+            for (uint32_t i = bHi + tid; i < m; i += blockDim.x) D[i] = base[phys_index(s, i)];
+            bulk = true;  // the phase completes either way
         }
+        for (uint32_t i = tid; i < m; i += blockDim.x) P0[i] = (uint16_t)i;
         if (tid == 0) sh.stack_top = 0;
         __syncthreads();
+        // D is complete (bulk copy arrived, the threads' parts behind the barrier above)
+        auto wait_data = [&]() -> bool {
+            if (!bulk) return true;
+            bulk = false;
+            const bool ok = __syncthreads_and(mbar_wait(&sh.load_bar, loads & 1u)) != 0;  // one verdict
+            ++loads;
+            if (!ok && tid == 0) report(args.status, RIP_ETIMEOUT, 0x5109, item);
+            return ok;
+        };
 
         bool in_place = false;  // D already holds the output order
         if (plan.is_leaf(m, s.level)) {
             if (m > 1 && m <= 64u * kThreads) {
                 fy_draws(P1, m, key, s.level, s.o);
+                if (!wait_data()) break;
                 // 32-bit reservations after D when they fit, else 16-bit ones in P0's place
                 const uint64_t mr = (m + 7u) & ~7u;
-                const uint64_t r32_off = 4 * mr + (args.medium ? 0 : (uint64_t)W * mr);
+                const uint64_t r32_off = 4 * mr + (args.medium ? 0 : (uint64_t)W * mr + 16);
                 if (r32_off + 4 * mr <= args.dyn_bytes)
                     fy_parallel_data(D, P1, reinterpret_cast<uint32_t*>(dyn + r32_off), m, args.status);
                 else
@@ -630,6 +695,7 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(SmallArgs args) {
             }
         }
         __syncthreads();
+        if (!wait_data()) break;
         if (in_place) {
             for (uint32_t i = tid; i < m; i += blockDim.x) base[s.o + i] = D[i];
         } else {
@@ -639,6 +705,7 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(SmallArgs args) {
                 else report(args.status, RIP_EINTERNAL, 0x5107, j);  // never read outside the subproblem
             }
         }
+        fence_proxy_async_smem();  // these reads of D come before the next bulk copy into it
         __syncthreads();
     }
 }
@@ -649,7 +716,7 @@ size_t small_fixed_smem() { return (sizeof(SmallShared) + 15) & ~size_t(15); }
 
 size_t small_smem_bytes(uint64_t m, uint32_t w, bool medium) {
     const uint64_t mr = (m + 7u) & ~7ull;
-    return small_fixed_smem() + 4 * mr + (medium ? 0 : w * mr);
+    return small_fixed_smem() + 4 * mr + (medium ? 0 : w * mr + 16);
 }
 
 cudaError_t launch_small(const SmallArgs& args_in, uint32_t w, size_t smem, uint32_t grid, cudaStream_t stream) {
