@@ -208,10 +208,11 @@ template <typename StartFn>
 __device__ void finish_children(SmallShared& sh, uint16_t* P0, uint16_t* X, uint16_t* Y, uint32_t a, uint32_t len,
                                 uint32_t k, uint32_t L, uint32_t buf, const DevPlan& plan, PhiloxKey key,
                                 uint64_t o_r, Status* status, StartFn start) {
-    // leaf children: partner draws first, by every thread (blockDim/k threads per child; the
-    // scatter's source range is free now and holds them), then one thread per child runs the
-    // child's swap chain
-    const uint32_t tpc = k >= blockDim.x ? 1u : blockDim.x / k;  // both powers of two
+    // leaf children: partner draws first, by every thread (tpc = blockDim/k threads per child;
+    // the scatter's source range is free now and holds them), then one thread per child runs
+    // the child's swap chain (consecutive threads: full warps measured faster than chains
+    // spread over all warps)
+    const uint32_t tpc = k >= blockDim.x ? 1u : blockDim.x / k;
     for (uint32_t b = threadIdx.x / tpc; b < k; b += blockDim.x / tpc) {
         const uint32_t sb = start(b);
         const uint32_t se = b + 1 < k ? start(b + 1) : len;
@@ -278,10 +279,15 @@ __device__ void finish_children(SmallShared& sh, uint16_t* P0, uint16_t* X, uint
 // low six bucket bits (one atomic OR per lane) and one ballot per higher bit
 // -- on GB300 a ballot costs more issue time than a shared atomic -- and the
 // lowest of them advances the warp's row (only the warp itself touches it).
-constexpr uint32_t kFastGroups = 24;  // groups per warp: 16 warps x 24 x 128 >= 48K + 3
+// Groups per warp of the single-tile scatter (its buckets stay in registers): enough for the
+// largest subproblem that fits in shared memory with w-byte elements (16 warps x G x 128
+// positions); larger ranges take the general path.
+__host__ __device__ constexpr uint32_t fast_groups(int W) { return W == 4 ? 16u : (W == 8 ? 12u : 8u); }
 
+template <uint32_t G>
 __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint32_t a, uint32_t len, uint32_t L,
-                                   uint32_t buf, const DevPlan& plan, PhiloxKey key, uint64_t sub_o, Status* status) {
+                                   uint32_t buf, const DevPlan& plan, PhiloxKey key, uint64_t sub_o, bool x_iota,
+                                   Status* status) {
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t k = plan.k[plan.idx(L)];
     const uint32_t kbits = log2_pow2(k);
@@ -291,7 +297,7 @@ __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, 
     const uint32_t delta = (uint32_t)(o_r & 3u);
     const uint64_t Q0 = o_r >> 2;
     const uint32_t ngroups = (len + delta + 127u) / 128u;
-    const uint32_t gpw = (ngroups + kWarps - 1) / kWarps;  // groups per warp (<= kFastGroups)
+    const uint32_t gpw = (ngroups + kWarps - 1) / kWarps;  // groups per warp (<= G)
     const uint32_t g0 = warp * gpw;
     uint16_t* hist = sh.f.hist;
     uint32_t* hist32 = reinterpret_cast<uint32_t*>(hist);  // two 16-bit counters per word
@@ -299,9 +305,9 @@ __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, 
     for (uint32_t j = tid; j < kWarps * 64u; j += blockDim.x) sh.f.mask[j] = 0;
     __syncthreads();
 
-    uint32_t bk[kFastGroups];  // 4 packed 8-bit buckets per group: lane l holds positions 4l .. 4l+3
+    uint32_t bk[G];  // 4 packed 8-bit buckets per group: lane l holds positions 4l .. 4l+3
 #pragma unroll
-    for (uint32_t g = 0; g < kFastGroups; ++g) {
+    for (uint32_t g = 0; g < G; ++g) {
         bk[g] = 0;
         if (g < gpw && g0 + g < ngroups) {
             const uint32_t vg = (g0 + g) * 128u;
@@ -345,7 +351,7 @@ __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, 
     uint16_t* row = hist + warp * 256u;
     uint32_t* mrow = sh.f.mask + warp * 64u;
 #pragma unroll
-    for (uint32_t g = 0; g < kFastGroups; ++g) {
+    for (uint32_t g = 0; g < G; ++g) {
         if (g < gpw && g0 + g < ngroups) {
             const uint32_t vg = (g0 + g) * 128u;
 #pragma unroll
@@ -377,7 +383,7 @@ __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, 
                 __syncwarp();
                 if (valid) {
                     const uint32_t d = base + __popc(peers & lt_mask);
-                    if (d < len) Y[a + d] = X[a + (v - delta)];
+                    if (d < len) Y[a + d] = x_iota ? (uint16_t)(a + (v - delta)) : X[a + (v - delta)];
                     else report(status, RIP_EINTERNAL, 0x5105, d);
                 }
             }
@@ -390,10 +396,12 @@ __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, 
 }
 
 // One scatter level of the range [a, a+len) (level L) from X into Y, both
-// index arrays; children ranges are finished (leaves) or pushed.
+// index arrays; children ranges are finished (leaves) or pushed.  x_iota: X
+// holds the identity there (the subproblem's first level; X is not read).
+template <uint32_t G>
 __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint32_t a, uint32_t len,
                               uint32_t L, uint32_t buf, const DevPlan& plan, PhiloxKey key,
-                              uint64_t sub_o, Status* status) {
+                              uint64_t sub_o, bool x_iota, Status* status) {
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t li = plan.idx(L);
     const uint32_t k = plan.k[li], B = plan.B[li];
@@ -411,8 +419,8 @@ __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint3
         if (tid == 0) report(status, RIP_EINTERNAL, 0x5101, ncnt);
         return;
     }
-    if (tiles == 1 && k <= 256 && (len + 3u + 127u) / 128u <= kWarps * kFastGroups) {
-        scatter_range_fast(sh, P0, P1, a, len, L, buf, plan, key, sub_o, status);
+    if (tiles == 1 && k <= 256 && (len + 3u + 127u) / 128u <= kWarps * G) {
+        scatter_range_fast<G>(sh, P0, P1, a, len, L, buf, plan, key, sub_o, x_iota, status);
         return;
     }
     for (uint32_t j = tid; j < ncnt; j += blockDim.x) sh.g.thr[j] = 0;
@@ -530,7 +538,7 @@ __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint3
                         report(status, RIP_EINTERNAL, 0x5103, d);
                         continue;
                     }
-                    Y[a + d] = X[a + i];
+                    Y[a + d] = x_iota ? (uint16_t)(a + i) : X[a + i];
                 }
                 __syncwarp();
                 // each warp reads only its own row: clear it for the next round
@@ -635,7 +643,6 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(SmallArgs args) {
             for (uint32_t i = bHi + tid; i < m; i += blockDim.x) D[i] = base[phys_index(s, i)];
             bulk = true;  // the phase completes either way
         }
-        for (uint32_t i = tid; i < m; i += blockDim.x) P0[i] = (uint16_t)i;
         if (tid == 0) sh.stack_top = 0;
         __syncthreads();
         // D is complete (bulk copy arrived, the threads' parts behind the barrier above)
@@ -662,7 +669,10 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(SmallArgs args) {
                     fy_parallel_data(D, P1, P0, m, args.status);
                 in_place = true;
             } else if (m > 1) {
+                for (uint32_t i = tid; i < m; i += blockDim.x) P0[i] = (uint16_t)i;  // fy_block permutes it
                 fy_block(P0, P1, m, key, s.level, s.o);
+            } else {
+                in_place = true;  // one element
             }
         } else {
             if (tid == 0) {
@@ -691,7 +701,7 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(SmallArgs args) {
                 const uint32_t L = (uint32_t)((e >> 40) & 0xFFu);
                 const uint32_t buf = (uint32_t)((e >> 48) & 1u);
                 __syncthreads();
-                scatter_range(sh, P0, P1, a, len, L, buf, plan, key, s.o, args.status);
+                scatter_range<fast_groups(W)>(sh, P0, P1, a, len, L, buf, plan, key, s.o, L == s.level, args.status);
             }
         }
         __syncthreads();
@@ -699,10 +709,25 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(SmallArgs args) {
         if (in_place) {
             for (uint32_t i = tid; i < m; i += blockDim.x) base[s.o + i] = D[i];
         } else {
-            for (uint32_t i = tid; i < m; i += blockDim.x) {
-                const uint32_t j = P0[i];
-                if (j < m) base[s.o + i] = D[j];
-                else report(args.status, RIP_EINTERNAL, 0x5107, j);  // never read outside the subproblem
+            // four independent gathers in flight per thread
+            for (uint32_t i0 = tid; i0 < m; i0 += 4u * blockDim.x) {
+                uint32_t j[4];
+                T v[4];
+#pragma unroll
+                for (uint32_t u = 0; u < 4; ++u) {
+                    const uint32_t i = i0 + u * blockDim.x;
+                    j[u] = i < m ? (uint32_t)P0[i] : 0u;
+                }
+#pragma unroll
+                for (uint32_t u = 0; u < 4; ++u)
+                    if (j[u] < m) v[u] = D[j[u]];
+#pragma unroll
+                for (uint32_t u = 0; u < 4; ++u) {
+                    const uint32_t i = i0 + u * blockDim.x;
+                    if (i >= m) break;
+                    if (j[u] < m) base[s.o + i] = v[u];
+                    else report(args.status, RIP_EINTERNAL, 0x5107, j[u]);  // never read outside the subproblem
+                }
             }
         }
         fence_proxy_async_smem();  // these reads of D come before the next bulk copy into it
