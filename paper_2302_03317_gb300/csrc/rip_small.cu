@@ -171,18 +171,27 @@ __device__ void fy_block(uint16_t* Z, uint16_t* draws, uint32_t len, PhiloxKey k
     __syncthreads();
 }
 
-// The four partner draws of the Philox call with counter q (positions 4q .. 4q+3) that fall in
-// steps [1, len) of the leaf starting at global position leaf_o; stored in H[step].
-__device__ __forceinline__ void fy_store_group(uint16_t* H, uint4 r, uint64_t q, uint32_t len, PhiloxKey key,
+// Partner draw of step i from word x when the multiply's low word fell below i + 1 (probability
+// below 2^-16 here): Lemire's exact rejection test, then the retry stream.  Kept out of line so
+// the common path stays short.
+__device__ __noinline__ uint32_t fy_draw_slow(uint32_t x, uint32_t i, PhiloxKey key, uint32_t L, uint64_t leaf_o) {
+    uint32_t v;
+    if (lemire32(x, i + 1, v)) return v;
+    return (uint32_t)fy_draw_retry(key, L, leaf_o, leaf_o + i, i + 1);
+}
+
+// The four partner draws of one Philox call whose first word belongs to step i0 (steps outside
+// [1, len) are skipped); stored in H[step].
+__device__ __forceinline__ void fy_store_group(uint16_t* H, uint4 r, int32_t i0, uint32_t len, PhiloxKey key,
                                                uint32_t L, uint64_t leaf_o) {
     const uint32_t w4[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
     for (uint32_t wd = 0; wd < 4; ++wd) {
-        const uint64_t i64 = 4 * q + wd - leaf_o;  // step index of this word
-        if (4 * q + wd < leaf_o + 1 || i64 >= len) continue;
-        const uint32_t i = (uint32_t)i64;
-        uint32_t v;
-        if (!lemire32(w4[wd], i + 1, v)) v = (uint32_t)fy_draw_retry(key, L, leaf_o, leaf_o + i, i + 1);
+        const int32_t si = i0 + (int32_t)wd;
+        if (si < 1 || si >= (int32_t)len) continue;
+        const uint32_t i = (uint32_t)si;
+        const uint64_t mw = (uint64_t)w4[wd] * (i + 1u);
+        const uint32_t v = (uint32_t)mw < i + 1u ? fy_draw_slow(w4[wd], i, key, L, leaf_o) : (uint32_t)(mw >> 32);
         H[i] = (uint16_t)v;
     }
 }
@@ -192,26 +201,25 @@ __device__ __forceinline__ void fy_store_group(uint16_t* H, uint4 r, uint64_t q,
 __device__ __forceinline__ void fy_draws_part(uint16_t* H, uint32_t len, PhiloxKey key, uint32_t L, uint64_t leaf_o,
                                               uint32_t sub, uint32_t step) {
     const uint64_t q_first = (leaf_o + 1) >> 2, q_last = (leaf_o + len - 1) >> 2;
+    const uint32_t ng = (uint32_t)(q_last - q_first) + 1u;
+    const int32_t i_first = (int32_t)(4 * q_first - leaf_o);  // step of the first group's word 0 (-2 .. 1)
     const uint32_t tag = L | (kTagFy << 8), o32 = (uint32_t)leaf_o;
-    for (uint64_t q = q_first + sub; q <= q_last; q += 2u * step) {
-        const uint64_t q2 = q + step;  // may lie past the leaf: computed, not stored
+    for (uint32_t g = sub; g < ng; g += 2u * step) {
+        const uint64_t q = q_first + g, q2 = q + step;  // q2 may lie past the leaf: computed, not stored
         const uint4 r = philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), tag, o32, key);
         const uint4 r2 = philox4x32_10((uint32_t)q2, (uint32_t)(q2 >> 32), tag, o32, key);
-        fy_store_group(H, r, q, len, key, L, leaf_o);
-        if (q2 <= q_last) fy_store_group(H, r2, q2, len, key, L, leaf_o);
+        fy_store_group(H, r, i_first + 4 * (int32_t)g, len, key, L, leaf_o);
+        if (g + step < ng) fy_store_group(H, r2, i_first + 4 * (int32_t)(g + step), len, key, L, leaf_o);
     }
 }
 
 // Children of a scattered range: leaves are finished right away, larger ones
 // are pushed for another scatter.  start(b) = first output index of bucket b.
+// Partner draws of the leaf children of a scattered range, by every thread (tpc = blockDim/k
+// threads per child), into the range's source array X (not read any more, or never read).
 template <typename StartFn>
-__device__ void finish_children(SmallShared& sh, uint16_t* P0, uint16_t* X, uint16_t* Y, uint32_t a, uint32_t len,
-                                uint32_t k, uint32_t L, uint32_t buf, const DevPlan& plan, PhiloxKey key,
-                                uint64_t o_r, Status* status, StartFn start) {
-    // leaf children: partner draws first, by every thread (tpc = blockDim/k threads per child;
-    // the scatter's source range is free now and holds them), then one thread per child runs
-    // the child's swap chain (consecutive threads: full warps measured faster than chains
-    // spread over all warps)
+__device__ void children_draws(uint16_t* X, uint32_t a, uint32_t len, uint32_t k, uint32_t L, const DevPlan& plan,
+                               PhiloxKey key, uint64_t o_r, StartFn start) {
     const uint32_t tpc = k >= blockDim.x ? 1u : blockDim.x / k;
     for (uint32_t b = threadIdx.x / tpc; b < k; b += blockDim.x / tpc) {
         const uint32_t sb = start(b);
@@ -221,7 +229,20 @@ __device__ void finish_children(SmallShared& sh, uint16_t* P0, uint16_t* X, uint
         if (size > 1 && plan.is_leaf(size, L + 1))
             fy_draws_part(X + a + sb, size, key, L + 1, o_r + sb, threadIdx.x % tpc, tpc);
     }
-    __syncthreads();
+}
+
+// draws_done: children_draws already ran (and a barrier followed).
+template <typename StartFn>
+__device__ void finish_children(SmallShared& sh, uint16_t* P0, uint16_t* X, uint16_t* Y, uint32_t a, uint32_t len,
+                                uint32_t k, uint32_t L, uint32_t buf, const DevPlan& plan, PhiloxKey key,
+                                uint64_t o_r, Status* status, bool draws_done, StartFn start) {
+    // leaf children: partner draws first (the scatter's source range is free now and holds
+    // them), then one thread per child runs the child's swap chain (consecutive threads: full
+    // warps measured faster than chains spread over all warps)
+    if (!draws_done) {
+        children_draws(X, a, len, k, L, plan, key, o_r, start);
+        __syncthreads();
+    }
     for (uint32_t b = threadIdx.x; b < k; b += blockDim.x) {
         const uint32_t sb = start(b);
         const uint32_t se = b + 1 < k ? start(b + 1) : len;
@@ -347,6 +368,9 @@ __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, 
         if ((j & 255u) < k) hist[j] = (uint16_t)(hist[j] + sh.f.start[j & 255u]);
     __syncthreads();
 
+    // X holds the identity and is not read: the children's partner draws go there now, so
+    // the Philox-heavy draws and the shared-memory-heavy ranking below overlap across warps
+    if (x_iota) children_draws(X, a, len, k, L, plan, key, o_r, [&](uint32_t b) { return sh.f.start[b]; });
     const uint32_t lt_mask = (1u << lane) - 1u;
     uint16_t* row = hist + warp * 256u;
     uint32_t* mrow = sh.f.mask + warp * 64u;
@@ -390,7 +414,7 @@ __device__ bool scatter_range_fast(SmallShared& sh, uint16_t* P0, uint16_t* P1, 
         }
     }
     __syncthreads();
-    finish_children(sh, P0, X, Y, a, len, k, L, buf, plan, key, o_r, status,
+    finish_children(sh, P0, X, Y, a, len, k, L, buf, plan, key, o_r, status, x_iota,
                     [&](uint32_t b) { return sh.f.start[b]; });
     return true;
 }
@@ -550,7 +574,8 @@ __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint3
     }
 
     // children: leaves now, larger ones onto the stack (tile 0 entry of fb = s_b)
-    finish_children(sh, P0, X, Y, a, len, k, L, buf, plan, key, o_r, status, [&](uint32_t b) { return sh.g.fb[b]; });
+    finish_children(sh, P0, X, Y, a, len, k, L, buf, plan, key, o_r, status, false,
+                    [&](uint32_t b) { return sh.g.fb[b]; });
 }
 
 template <int W>
