@@ -55,20 +55,21 @@ struct ClsMisc {
     uint32_t scan[32];
 };
 
-// Lanes of the warp with the same bucket as the calling lane (among valid lanes): one
-// ballot per bucket bit; KB > 0 fixes the bit count at compile time.
+// Lanes of the warp whose buckets agree with the calling lane's in the bits above the low
+// five (the low five are matched through a shared-memory mask row): one ballot per bit;
+// KB > 0 fixes the bit count at compile time.
 template <int KB>
-__device__ __forceinline__ uint32_t bucket_peers(uint32_t b, bool valid, uint32_t kbits) {
-    uint32_t peers = __ballot_sync(0xffffffffu, valid);
+__device__ __forceinline__ uint32_t bucket_peers_hi(uint32_t b, uint32_t kbits) {
+    uint32_t peers = 0xffffffffu;
     if constexpr (KB > 0) {
 #pragma unroll
-        for (int i = 0; i < KB; ++i) {
+        for (int i = 5; i < KB; ++i) {
             const bool bit = (b >> i) & 1u;
             const uint32_t m = __ballot_sync(0xffffffffu, bit);
             peers &= bit ? m : ~m;
         }
     } else {
-        for (uint32_t i = 0; i < kbits; ++i) {
+        for (uint32_t i = 5; i < kbits; ++i) {
             const bool bit = (b >> i) & 1u;
             const uint32_t m = __ballot_sync(0xffffffffu, bit);
             peers &= bit ? m : ~m;
@@ -117,6 +118,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
     uint64_t* jloc = optr + k;   // location of the block holding the round's first chunk
     uint64_t* pbase = jloc + k;  // pool location of the round's first pool block
     uint64_t* flist = reinterpret_cast<uint64_t*>(smem_raw + g.off_flist);  // 2 x k flush entries
+    uint32_t* masks = reinterpret_cast<uint32_t*>(smem_raw + g.off_mask);  // per ranking warp: 32 lane masks
     T* stage = reinterpret_cast<T*>(smem_raw + g.off_stage);
     T* bufs = reinterpret_cast<T*>(smem_raw + g.off_buf);
 
@@ -133,6 +135,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
     const bool flush_vec = a.vec16 && (Bs * W) % 16u == 0;
     T* pool = reinterpret_cast<T*>(a.pool);
 
+    for (uint32_t j = tid; j < nwr * 32u; j += blockDim.x) masks[j] = 0;  // kept zero after every step
     if (tid == 0) {
         for (uint32_t i = 0; i < nbuf; ++i) mbar_init(&ms.full[i], 1);
         mbar_init(&ms.stage_free, 1);
@@ -307,11 +310,21 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                         const uint32_t v = v0 + 32u * s;
                         const bool valid = interior || (v >= delta && v - delta < r);
                         const uint32_t b = bucket_of(group_step_word(words, s), k);
-                        const uint32_t peers = bucket_peers<KB>(b, valid, kbits);
+                        // lanes with the same bucket: the low five bits through the warp's mask
+                        // row (one shared atomic OR per lane), the higher ones by ballot -- on
+                        // GB300 a ballot costs more issue time than the shared-memory round trip
+                        uint32_t* mk = masks + warp * 32u + (b & 31u);
+                        if (valid) atomicOr(mk, 1u << lane);
+                        uint32_t peers = bucket_peers_hi<KB>(b, kbits);
+                        __syncwarp();
                         uint16_t* c = tbl + b * S + warp;
+                        peers &= valid ? *mk : 0u;
                         const uint32_t pre = valid ? (uint32_t)*c : 0u;
                         __syncwarp();
-                        if (valid && (peers & lt_mask) == 0) *c = (uint16_t)(pre + (uint32_t)__popc(peers));
+                        if (valid && (peers & lt_mask) == 0) {
+                            *c = (uint16_t)(pre + (uint32_t)__popc(peers));
+                            *mk = 0u;  // every bucket sharing the entry clears it: same value
+                        }
                         __syncwarp();
                         if (valid) packed[s] = b | ((pre + (uint32_t)__popc(peers & lt_mask)) << 10);
                     }
@@ -611,6 +624,8 @@ bool classify_config(uint32_t k, uint32_t B, uint32_t w, ClsCfg* out) {
     off = a16(off + (size_t)k * 3 * 8);
     c.off_flist = (uint32_t)off;
     off = a16(off + (size_t)k * 2 * 8);
+    c.off_mask = (uint32_t)off;
+    off = a16(off + (size_t)c.nwr * 32 * 4);
     const size_t fixed = off;
     const size_t buf_bytes = a16((size_t)c.bufstride * w);
     uint32_t best_d = 0, best_nbuf = 0;

@@ -95,7 +95,7 @@ struct ClsCfg {
     uint32_t q;          // elements per 16 bytes
     uint32_t nbuf;       // input buffers (2 or 3)
     uint32_t bufstride;  // elements per input buffer
-    uint32_t off_tbl, off_u32, off_u64, off_flist, off_stage, off_buf, bytes;
+    uint32_t off_tbl, off_u32, off_u64, off_flist, off_mask, off_stage, off_buf, bytes;
 };
 
 struct LevelArgs {
