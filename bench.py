@@ -35,8 +35,9 @@ if ROOT not in sys.path:
 
 METRIC = "shuffled elems/s and % HBM roofline (2^30 u64); batched vs plain elems/s"
 # dram__bytes_read + dram__bytes_write per element of one launch, from the ncu captures
-# summarised in profiles/classify_shuffle_2pow26_u64.md and profiles/permute_shuffle_2pow26_u64.md
-DRAM_BYTES_PER_ELEM = {"classify": 13.3, "permute": 13.5}
+# summarised in profiles/classify_shuffle_2pow26_u64.md, profiles/permute_shuffle_2pow26_u64.md
+# and profiles/solver_shuffle_2pow26_u64.md (root-level launches and the leaf solver at 2^26 u64)
+DRAM_BYTES_PER_ELEM = {"classify": 15.2, "permute": 15.9, "solve_small": 15.1}
 UNIT = "elems/s"
 N_LOG2 = 30
 ELEM_BYTES = 8
