@@ -85,8 +85,11 @@ typedef struct {
 /* Fills *plan with the library's default plan for n elements of elem_bytes:
  * k = 256 (k = 64 below 128 MiB of data, the paper's rule in Sec. 5), base
  * 4096, B sized so k*B*elem_bytes = 128 KiB, the root tile chosen so that the
- * root has one tile per streaming multiprocessor and deeper levels one tile
- * per subproblem.  Returns RIP_EINVAL for a NULL plan or bad elem_bytes. */
+ * root has one tile per streaming multiprocessor; where level 1 runs in place
+ * (root children above 32K elements) its tile is 6/7 of the expected child, so
+ * every child has a long and a short tile (the short ones keep the SMs busy
+ * while a wave's long ones run), else one tile per subproblem.  Returns
+ * RIP_EINVAL for a NULL plan or bad elem_bytes. */
 int rip_default_plan(uint64_t n, uint32_t elem_bytes, rip_plan *plan);
 
 /* Fills *plan with a plan for inputs that fill most of the device (the

@@ -102,7 +102,7 @@ struct LevelCaps {
 struct Layout {
     size_t total = 0;
     size_t arrays, lists_big0, lists_big1, small, medium, bigfy, counts, counters, pool_used;
-    size_t tiles, sp_tile_begin, segs, C, FBc, TLc, tinfo, child, words, pool, dem, parks, mscratch;
+    size_t tiles, sched, sp_tile_begin, segs, C, FBc, TLc, tinfo, child, words, pool, dem, parks, mscratch;
     uint32_t big_cap, small_cap, medium_cap, bigfy_cap, tile_cap, dem_cap, park_cap, levels, wave_cap;
     uint32_t medium_grid;
     uint64_t pair_cap, child_cap, pool_cap, slot_cap;
@@ -340,6 +340,7 @@ Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& 
     L.pool_used = take(sizeof(uint64_t));
     const size_t meta_start = off;
     L.tiles = take(sizeof(TileRef) * L.tile_cap);
+    L.sched = take(sizeof(uint32_t) * L.tile_cap);
     L.sp_tile_begin = take(sizeof(uint32_t) * L.wave_cap);
     L.segs = take(sizeof(SegDesc) * L.wave_cap);
     L.C = take(sizeof(uint32_t) * L.pair_cap);
@@ -370,7 +371,11 @@ bool default_plan_impl(uint64_t n, uint32_t w, rip_plan* p, uint32_t num_sms) {
     const uint32_t k = bytes < (128ull << 20) ? 64 : 256;  // Sec. 5: k = 64 below 128 MiB, else 256
     uint32_t B = (uint32_t)((128u * 1024u) / (k * w));
     B = std::max<uint32_t>(1, std::min<uint32_t>(B, 1024));
-    // level 0: one tile per SM (rounded to a multiple of B); deeper levels: one tile per subproblem
+    // level 0: one tile per SM (rounded to a multiple of B); deeper levels: one tile per subproblem,
+    // or, where level 1 runs in place, two: the first 6/7 of the expected subproblem and the rest.
+    // Classify takes all first tiles before the short ones, so when a wave holds fewer
+    // subproblems than SMs the idle SMs work through the short tiles meanwhile (measured on
+    // GB300 at 2^30 u64: 128 subproblems per wave on 152 SMs)
     uint64_t T0 = (n + num_sms - 1) / std::max<uint32_t>(num_sms, 1);
     T0 = std::max<uint64_t>(T0, (uint64_t)B * 64);
     T0 = (T0 + B - 1) / B * B;
@@ -393,6 +398,7 @@ bool default_plan_impl(uint64_t n, uint32_t w, rip_plan* p, uint32_t num_sms) {
     p->level[1].k = k1;
     p->level[1].block = B;
     p->level[1].tile = std::min<uint64_t>((uint64_t)B << 20, (uint64_t)1 << 40) / B * B;
+    if (m1 > 32768) p->level[1].tile = std::max<uint64_t>((uint64_t)B * 64, (6 * m1 / 7 + B - 1) / B * B);
     p->base = 4096;
     p->max_levels = 0;
     return true;
@@ -581,6 +587,7 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
         a.small_max_m = lay.small_max_m;
         a.tiles = reinterpret_cast<TileRef*>(wsp + lay.tiles);
         a.sp_tile_begin = reinterpret_cast<uint32_t*>(wsp + lay.sp_tile_begin);
+        a.sched = reinterpret_cast<uint32_t*>(wsp + lay.sched);
         a.counters = counters;
         a.pool_used = pool_used;
         a.tile_cap = lay.tile_cap;

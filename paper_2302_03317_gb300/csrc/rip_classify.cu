@@ -149,7 +149,10 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
     // one per tile), flush_ready (one per round); every thread counts the same way
     uint32_t grc = 0, sfc = 0, frc = 0;
     for (;;) {
-        if (tid == 0) ms.tile = atomicAdd(&a.counters[1], 1u);
+        if (tid == 0) {
+            const uint32_t c = atomicAdd(&a.counters[1], 1u);
+            ms.tile = c < ntiles ? a.sched[c] : c;
+        }
         __syncthreads();
         const uint32_t tile = ms.tile;
         if (tile >= ntiles || ms.fail) break;

@@ -124,6 +124,7 @@ struct LevelArgs {
     TileRef* tiles;
     uint32_t wb, wcap, wend;  // this wave: big-list entries [wb, wb + wcap); all waves: [0, wend)
     uint32_t* sp_tile_begin;  // per subproblem of the wave
+    uint32_t* sched;          // classify order of the tiles: every subproblem's non-last tiles, then the last ones
     SegDesc* segs;            // per subproblem of the wave
     uint64_t slot_cap;        // entries of the slot-word table
     uint32_t* counters;       // [0] tiles, [1] tile cursor, [2] demoted count, [4..5] chunk cursor, [6] parks,

@@ -144,6 +144,17 @@ __global__ void tiles_kernel(LevelArgs a) {
         }
         __syncthreads();
     }
+    // the order classify takes the tiles in: all non-last tiles (full size) first, then every
+    // subproblem's last, usually smaller, tile -- the short tiles fill the SMs that the long
+    // ones leave idle when a wave has fewer subproblems than SMs
+    if (carry <= a.tile_cap) {
+        for (uint32_t i = threadIdx.x; i < we; i += blockDim.x) {
+            const uint32_t begin = a.sp_tile_begin[i];
+            const uint32_t end = i + 1 < we ? a.sp_tile_begin[i + 1] : carry;
+            for (uint32_t t = begin; t + 1 < end; ++t) a.sched[t - i] = t;
+            if (end > begin) a.sched[carry - we + i] = end - 1;
+        }
+    }
     if (threadIdx.x == 0) {
         bool ok = true;
         if (carry > a.tile_cap) {
