@@ -186,7 +186,7 @@ int rip_last_call_info(uint64_t out[3]);
  * performs no allocation.  Inputs whose workspace
  * (rip_shuffle_workspace_size) exceeds the array are rejected with
  * RIP_ETOOLARGE before anything is enqueued; with the default plans every
- * power-of-two size up to 2^28 4-byte, 2^26 8-byte and 2^20 16-byte elements
+ * power-of-two size up to 2^27 4-byte, 2^26 8-byte and 2^20 16-byte elements
  * fits (the workspace is not monotone in n: ask rip_shuffle_workspace_size).  The first call
  * on a device looks up the array's device address (a one-time set-up); make
  * that first call before any stream capture.  All calls share the array and
