@@ -15,13 +15,14 @@
 //            ragged edges (unaligned ends, the rotation's wrap piece) are
 //            copied by the threads
 //   rank     Philox bucket draws (a1), stable ranks per bucket: the lanes of a
-//            step with the same bucket come from one ballot per bucket bit,
-//            the warp's running count per bucket lives in a (bucket, warp)
-//            table of 16-bit counters (a2)
+//            step with the same bucket come from a 32-entry shared-memory mask
+//            row per warp (indexed by the low five bucket bits) and one ballot
+//            per higher bit; the warp's running count per bucket lives in a
+//            (bucket, warp) table of 16-bit counters (a2)
 //            -- meanwhile the chunks completed by the previous round are
 //               written out, so stores overlap the arithmetic
-//   book     per bucket: exclusive prefix over the ranking warps (one warp
-//            scans 32/nwr buckets at once), blocks completed, home slots or
+//   book     per bucket: exclusive prefix over the ranking warps (one lane
+//            per bucket, 32 buckets per warp), blocks completed, home slots or
 //            pool blocks for blocks that receive data, slot words
 //   place    every element goes to its bucket's shared-memory chunk (Bs
 //            elements, Bs divides B), straight to its block in global memory

@@ -84,6 +84,25 @@ def test_one_level_in_place_records():
     check(60_000, 16, rip.Plan(ks=[32], Ts=[4096], Bs=[128], base=4096), seed=1)
 
 
+# The on-SM solver brings a subproblem in by bulk copies of the 16-byte-aligned middle of each
+# rotation piece and copies the ragged rest by threads: views that start off a 16-byte boundary
+# (every residue for 4- and 8-byte elements), a root leaf (one piece), a root scattered inside
+# the SM, and children of an in-place level (rotated: two pieces, each with its own alignment).
+@pytest.mark.parametrize("w,offset", [(4, 1), (4, 2), (4, 3), (8, 1)])
+@pytest.mark.parametrize("n,plan", [(20_000, FY), (25_000, SMEM1), (300_000, INPLACE2), (299_999, INPLACE1)])
+def test_unaligned_views_through_the_solver(n, w, offset, plan):
+    check(n, w, plan, seed=41 + offset, offset=offset)
+
+
+def test_records_need_16_byte_alignment():
+    # elem_bytes = 16 requires 16-byte-aligned data: an 8-byte-offset view is rejected on the host
+    flat = torch.zeros(2 * 1000 + 2, dtype=torch.int64, device="cuda")
+    view = flat[1:1 + 2 * 1000].view(1000, 2)
+    with pytest.raises(Exception):
+        rip.shuffle_(view, 1)
+    assert int(flat.abs().sum()) == 0  # nothing was written
+
+
 @pytest.mark.parametrize("n,w", [(1 << 21, 8), (1_500_001, 4)])
 def test_two_levels_in_place(n, w):
     check(n, w, INPLACE2, seed=7)
