@@ -9,8 +9,8 @@ library's default plan (k = 256, base 4096).  Prints one JSON line (rank 0):
 value = shuffled elements per second over all ranks; "roofline" for the
 dominant kernel (algorithmic bytes / CUDA-event launch time vs the measured
 HBM copy bandwidth); "cpu_baseline" = the CPU oracle on a bounded sample;
-"e2e" = the same shuffle with the array copied from and back to pinned host
-memory inside the timed region.  N > 1: one independent replica per GPU
+"e2e" = the same shuffle with every step's array copied from and back to pinned
+host memory inside the timed region (steps pipelined over two buffers).  N > 1: one independent replica per GPU
 (the method does not exchange data between GPUs in this build), launched
 with torchrun; the timed region is bracketed by barriers and the slowest
 rank's time is used.
@@ -457,27 +457,51 @@ def main():
     whole_roof_ms = (scatter_levels + 1) * 2 * n * w / (hbm_gbs * 1e9) * 1e3
     kernel_table = {k: {"launches": v[0], "ms_per_step": v[1] / args.steps} for k, v in sorted(prof.items())}
 
-    # end to end through the C ABI: pinned host array -> device, shuffle, -> host
+    # end to end through the C ABI: every step uploads its array from pinned host memory, shuffles
+    # it and downloads the result.  Steps are pipelined over two device and two host buffers on
+    # three streams (upload, shuffle, download): step i+1's upload and step i-1's download run
+    # during step i's shuffle (the host link is full duplex and its copies take about 3 % of HBM
+    # bandwidth).  The timed region runs from the first upload to the last download, so it
+    # includes the pipeline's fill and drain; every byte crosses the link every step.
     e2e = None
     if not args.no_e2e and not capacity:
-        host = torch.empty(n, dtype=torch.int64, pin_memory=True)
-        host.copy_(x)
+        hosts = [torch.empty(n, dtype=torch.int64, pin_memory=True) for _ in range(2)]
+        for h in hosts:
+            h.copy_(x)
+        devs = [x, torch.empty_like(x)]
+        s_up, s_sh, s_dn = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
         torch.cuda.synchronize()
         barrier()
         h0 = torch.cuda.Event(enable_timing=True)
         h1 = torch.cuda.Event(enable_timing=True)
-        h0.record(stream)
+        down_done = [None, None]
+        h0.record(s_up)
         for i in range(args.steps):
-            x.copy_(host, non_blocking=True)
-            rip.shuffle_(x, SEED + 2000 + i, plan=plan)
-            host.copy_(x, non_blocking=True)
-        h1.record(stream)
+            b = i % 2
+            if down_done[b] is not None:  # buffers b are free once step i-2 has come back
+                s_up.wait_event(down_done[b])
+            with torch.cuda.stream(s_up):
+                devs[b].copy_(hosts[b], non_blocking=True)
+            up_done = torch.cuda.Event()
+            up_done.record(s_up)
+            s_sh.wait_event(up_done)
+            rip.shuffle_(devs[b], SEED + 2000 + i, plan=plan, stream=s_sh)
+            sh_done = torch.cuda.Event()
+            sh_done.record(s_sh)
+            s_dn.wait_event(sh_done)
+            with torch.cuda.stream(s_dn):
+                hosts[b].copy_(devs[b], non_blocking=True)
+            down_done[b] = torch.cuda.Event()
+            down_done[b].record(s_dn)
+        h1.record(s_dn)
         torch.cuda.synchronize()
         barrier()
         e_ms = max_over_ranks(h0.elapsed_time(h1) / args.steps, dist, "cuda")
         e2e = {"value": job_rate(ws, n, e_ms), "unit": UNIT, "h2d_bytes_per_step": n * w,
-               "d2h_bytes_per_step": n * w, "ms_per_step": e_ms}
-        del host
+               "d2h_bytes_per_step": n * w, "ms_per_step": e_ms,
+               "how": "pinned host -> device, shuffle, -> host every step; steps pipelined over two buffers "
+                      "(upload, shuffle, download streams); fill and drain inside the timed region"}
+        del hosts, devs
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and not capacity:
