@@ -44,6 +44,18 @@ __device__ __forceinline__ U ld_cg(const U* p) {
     return __ldcg(p);
 }
 
+template <typename U>
+__device__ __forceinline__ void cp_async_unit(U* dst, const U* src) {
+    static_assert(sizeof(U) == 4 || sizeof(U) == 8 || sizeof(U) == 16, "cp.async sizes");
+    if constexpr (sizeof(U) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst)), "l"(src), "n"(sizeof(U))
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ bool push_sub(Sub* list, uint32_t* count, uint32_t cap, const Sub& s, Status* st,
                                          uint32_t where) {
     const uint32_t i = atomicAdd(count, 1u);
@@ -290,7 +302,8 @@ __global__ void __launch_bounds__(kPermuteThreads, 4) permute_kernel(LevelArgs a
     const uint32_t gmask = 0xFFu << ((tid & 31u) & ~(kGroup - 1u));
     const uint32_t leader_lane = (tid & 31u) & ~(kGroup - 1u);
     const bool leader = lg == 0;
-    U* buf = reinterpret_cast<U*>(smem_raw) + (size_t)g * units;
+    U* slots = reinterpret_cast<U*>(smem_raw) + (size_t)g * 2u * units;  // carried block, incoming block
+    uint32_t cs = 0;  // slot of the carried block
     const uint64_t slot_bytes = (uint64_t)a.B * w;
 
     bool carrying = false;
@@ -353,6 +366,7 @@ __global__ void __launch_bounds__(kPermuteThreads, 4) permute_kernel(LevelArgs a
                 if (leader) report(a.status, RIP_EINTERNAL, 0x6407, s);
                 continue;
             }
+            U* buf = slots + cs * units;
             for (uint32_t u = lg; u < units; u += kGroup) buf[u] = ld_cg(sp + u);
             __syncwarp(gmask);  // every lane's read of slot s has returned
             if (leader) st_release(&a.words[s], 0u);
@@ -375,6 +389,7 @@ __global__ void __launch_bounds__(kPermuteThreads, 4) permute_kernel(LevelArgs a
                 continue;
             }
             U* dst = reinterpret_cast<U*>(a.pool + rec.pool_off * w);
+            const U* buf = slots + cs * units;
             for (uint32_t u = lg; u < units; u += kGroup) dst[u] = buf[u];
             __syncwarp(gmask);
             carrying = false;
@@ -410,6 +425,7 @@ __global__ void __launch_bounds__(kPermuteThreads, 4) permute_kernel(LevelArgs a
             if (ok) {
                 off = __shfl_sync(gmask, off, leader_lane);
                 U* dst = reinterpret_cast<U*>(a.pool + off * w);
+                const U* buf = slots + cs * units;
                 for (uint32_t u = lg; u < units; u += kGroup) dst[u] = buf[u];
                 __syncwarp(gmask);
                 carrying = false;
@@ -417,12 +433,11 @@ __global__ void __launch_bounds__(kPermuteThreads, 4) permute_kernel(LevelArgs a
             }
             steps = 0x80000000u;  // no room: finish this chain without parking
         }
-        U y[4];
-#pragma unroll
-        for (uint32_t j = 0; j < 4; ++j) {
-            const uint32_t u = lg + j * kGroup;
-            if (u < units) y[j] = ld_cg(dp + u);
-        }
+        // the block at d, read ahead of the claim into the incoming slot (only this group writes d)
+        U* buf = slots + cs * units;
+        U* inc = slots + (cs ^ 1u) * units;
+        for (uint32_t u = lg; u < units; u += kGroup) cp_async_unit(inc + u, dp + u);
+        cp_async_commit();
         uint32_t old = 0;
         if (leader) old = atom_or_acquire(&a.words[d], kWordTaken);
         old = __shfl_sync(gmask, old, leader_lane);
@@ -440,6 +455,7 @@ __global__ void __launch_bounds__(kPermuteThreads, 4) permute_kernel(LevelArgs a
                 }
             }
             spins = __shfl_sync(gmask, spins, leader_lane);
+            cp_async_wait_all();  // the incoming slot is reloaded on the next try
             if (spins > (1u << 24)) {
                 carrying = false;  // give up; the error is reported
                 continue;
@@ -447,22 +463,12 @@ __global__ void __launch_bounds__(kPermuteThreads, 4) permute_kernel(LevelArgs a
             __syncwarp(gmask);
             continue;
         }
+        cp_async_wait_all();  // this lane's units of the block at d are in the incoming slot
         if (old & kWordOcc) {
-            // swap: read the block at d, write ours, carry the one read
-#pragma unroll
-            for (uint32_t j = 0; j < 4; ++j) {
-                const uint32_t u = lg + j * kGroup;
-                if (u < units) {
-                    dp[u] = buf[u];
-                    buf[u] = y[j];
-                }
-            }
-            for (uint32_t u = lg + 4 * kGroup; u < units; u += kGroup) {
-                const U t = ld_cg(dp + u);
-                dp[u] = buf[u];
-                buf[u] = t;
-            }
+            // swap: write ours to d, carry the block read from it
+            for (uint32_t u = lg; u < units; u += kGroup) dp[u] = buf[u];
             __syncwarp(gmask);
+            cs ^= 1u;
             dw = old;
             ++steps;
         } else {
@@ -612,8 +618,18 @@ __global__ void bigfy_kernel(const Sub* list, const uint32_t* count, uint32_t ca
 
 }  // namespace
 
+// Threads of a permutation CTA: every kGroup lanes move one block and hold two B-element slots
+// in shared memory (the carried block and the next one, read ahead); large blocks get fewer
+// groups per CTA.  0: a single group's slots do not fit.
+uint32_t permute_threads(uint32_t B, uint32_t w) {
+    const size_t per_group = 2ull * B * w;
+    const size_t groups = per_group ? kSmemOptin / per_group : 0;
+    const size_t threads = std::min<size_t>(kPermuteThreads, groups * kGroup) / 32u * 32u;
+    return (uint32_t)threads;
+}
+
 size_t permute_smem_bytes(uint32_t B, uint32_t w) {
-    return (size_t)(kPermuteThreads / kGroup) * B * w;
+    return (size_t)(permute_threads(B, w) / kGroup) * 2u * B * w;
 }
 
 cudaError_t launch_init(const InitArgs& a, cudaStream_t s) {
@@ -639,18 +655,21 @@ static cudaError_t launch_level_w(const LevelArgs& a, uint32_t num_sms, cudaStre
         ProfScope p("resolve", s);
         resolve_kernel<<<num_sms * 4, 256, 0, s>>>(a);
     }
+    const uint32_t pthreads = permute_threads(a.B, W);
+    if (pthreads == 0) return cudaErrorInvalidConfiguration;  // a block of more than 113 KB
     const size_t psm = permute_smem_bytes(a.B, W);
+    const uint32_t pgrid = num_sms * 8u * (kPermuteThreads / pthreads);
     if (a.vec16) {
         err = cudaFuncSetAttribute(permute_kernel<uint4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
         if (err != cudaSuccess) return err;
         ProfScope p("permute", s);
-        permute_kernel<uint4><<<num_sms * 8, kPermuteThreads, psm, s>>>(a, W);
+        permute_kernel<uint4><<<pgrid, pthreads, psm, s>>>(a, W);
     } else {
         using T = typename Elem<W>::T;
         err = cudaFuncSetAttribute(permute_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
         if (err != cudaSuccess) return err;
         ProfScope p("permute", s);
-        permute_kernel<T><<<num_sms * 8, kPermuteThreads, psm, s>>>(a, W);
+        permute_kernel<T><<<pgrid, pthreads, psm, s>>>(a, W);
     }
     {
         ProfScope p("parked", s);
