@@ -37,7 +37,7 @@ METRIC = "shuffled elems/s and % HBM roofline (2^30 u64); batched vs plain elems
 # dram__bytes_read + dram__bytes_write per element of one launch, from the ncu captures
 # summarised in profiles/classify_shuffle_2pow26_u64.md, profiles/permute_shuffle_2pow26_u64.md
 # and profiles/solver_shuffle_2pow26_u64.md (root-level launches and the leaf solver at 2^26 u64)
-DRAM_BYTES_PER_ELEM = {"classify": 15.2, "permute": 15.9, "solve_small": 15.1}
+DRAM_BYTES_PER_ELEM = {"classify": 15.2, "permute": 15.6, "solve_small": 15.1}
 UNIT = "elems/s"
 N_LOG2 = 30
 ELEM_BYTES = 8
@@ -120,6 +120,31 @@ def max_over_ranks(ms: float, dist=None, device=None) -> float:
     t = torch.tensor([ms], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def _bind_to_gpu_cpus(device_index: int):
+    """Binds this process to the CPUs next to the GPU (sysfs local_cpulist of its PCI device), so
+    that host memory it allocates lands on the GPU's NUMA node; returns the CPU list or None."""
+    import torch
+    try:
+        p = torch.cuda.get_device_properties(device_index)
+        bus = f"{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        with open(f"/sys/bus/pci/devices/{bus}/local_cpulist") as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            if "-" in part:
+                lo, hi = part.split("-")
+                cpus.update(range(int(lo), int(hi) + 1))
+            elif part:
+                cpus.add(int(part))
+        cpus &= os.sched_getaffinity(0)
+        if not cpus:
+            return None
+        os.sched_setaffinity(0, cpus)
+        return spec
+    except Exception:  # no sysfs entry or no permission: leave the placement to the OS
+        return None
 
 
 def job_rate(world_size: int, n_per_rank: int, ms_per_step: float) -> float:
@@ -465,6 +490,8 @@ def main():
     # includes the pipeline's fill and drain; every byte crosses the link every step.
     e2e = None
     if not args.no_e2e and not capacity:
+        # pinned buffers on the GPU's own NUMA node: allocate from a thread bound to its CPUs
+        numa = _bind_to_gpu_cpus(local)
         hosts = [torch.empty(n, dtype=torch.int64, pin_memory=True) for _ in range(2)]
         for h in hosts:
             h.copy_(x)
@@ -500,7 +527,8 @@ def main():
         e2e = {"value": job_rate(ws, n, e_ms), "unit": UNIT, "h2d_bytes_per_step": n * w,
                "d2h_bytes_per_step": n * w, "ms_per_step": e_ms,
                "how": "pinned host -> device, shuffle, -> host every step; steps pipelined over two buffers "
-                      "(upload, shuffle, download streams); fill and drain inside the timed region"}
+                      "(upload, shuffle, download streams); fill and drain inside the timed region",
+               "host_cpus": numa}
         del hosts, devs
 
     cpu = None
