@@ -67,7 +67,7 @@ enum {
  * canonical tile/block layout described above). */
 typedef struct {
     uint32_t k;     /* buckets: power of two, 2 <= k <= 1024                   */
-    uint32_t block; /* B >= 1 elements per full block                           */
+    uint32_t block; /* B >= 1 elements per full block; B * elem_bytes <= 29 KiB  */
     uint64_t tile;  /* T >= B, T % B == 0 (tiles start at each subproblem start) */
 } rip_level_params;
 

@@ -144,6 +144,7 @@ int validate_plan(const rip_plan& p, uint32_t w) {
         if (q.block < 1 || q.tile < q.block || q.tile % q.block) return RIP_EINVAL;
         ClsCfg cc;
         if (!classify_config(q.k, q.block, w, &cc)) return RIP_EINVAL;
+        if (permute_threads(q.block, w) == 0) return RIP_EINVAL;  // two block slots per group must fit
         if (l > 0 && p.level[l - 1].block % q.block) return RIP_EINVAL;  // slot grids must nest
     }
     return RIP_OK;

@@ -196,6 +196,7 @@ cudaError_t launch_classify(const LevelArgs& a, uint32_t w, uint32_t num_sms, cu
 
 // rip_level.cu
 size_t permute_smem_bytes(uint32_t B, uint32_t w);
+uint32_t permute_threads(uint32_t B, uint32_t w);
 cudaError_t launch_init(const InitArgs& a, cudaStream_t s);
 cudaError_t launch_level(const LevelArgs& a, uint32_t w, uint32_t num_sms, cudaStream_t s, uint32_t* launches);
 cudaError_t launch_bigfy(const Sub* list, const uint32_t* count, uint32_t cap, const ArrayDesc* arrays,
