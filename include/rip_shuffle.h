@@ -86,7 +86,7 @@ typedef struct {
  * k = 256 (k = 64 below 128 MiB of data, the paper's rule in Sec. 5), base
  * 4096, B sized so k*B*elem_bytes = 128 KiB, the root tile chosen so that the
  * root has one tile per streaming multiprocessor; where level 1 runs in place
- * (root children above 32K elements) its tile is 6/7 of the expected child, so
+ * (root children above 32K elements) its tile is 4/5 of the expected child, so
  * every child has a long and a short tile (the short ones keep the SMs busy
  * while a wave's long ones run), else one tile per subproblem.  Returns
  * RIP_EINVAL for a NULL plan or bad elem_bytes. */
