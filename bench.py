@@ -147,6 +147,45 @@ def _bind_to_gpu_cpus(device_index: int):
         return None
 
 
+def _pinned_host_buffers(n: int, count: int):
+    """count pinned int64 host buffers of n elements: anonymous mappings advised to use 2 MiB
+    pages and registered with cudaHostRegister (few address translations for the copy engines),
+    else torch's pinned allocator.  Returns (tensors, kind, mappings)."""
+    import mmap
+
+    import torch
+    tensors, regions = [], []
+    try:
+        cudart = torch.cuda.cudart()
+        for _ in range(count):
+            m = mmap.mmap(-1, n * 8, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
+            regions.append(m)
+            if hasattr(mmap, "MADV_HUGEPAGE"):
+                m.madvise(mmap.MADV_HUGEPAGE)
+            t = torch.frombuffer(m, dtype=torch.int64)
+            t.fill_(0)
+            if cudart.cudaHostRegister(t.data_ptr(), n * 8, 0) != cudart.cudaError.success:
+                raise RuntimeError("cudaHostRegister failed")
+            tensors.append(t)
+        return tensors, "2 MiB-page mappings registered with cudaHostRegister", regions
+    except Exception:
+        _release_host_buffers(tensors, regions)
+        return [torch.empty(n, dtype=torch.int64, pin_memory=True) for _ in range(count)], "torch pin_memory", []
+
+
+def _release_host_buffers(tensors, regions):
+    import torch
+    if regions:
+        for t in tensors:
+            torch.cuda.cudart().cudaHostUnregister(t.data_ptr())
+        tensors.clear()
+        for m in regions:
+            try:
+                m.close()
+            except BufferError:  # a tensor still views it: left to the garbage collector
+                pass
+
+
 def job_rate(world_size: int, n_per_rank: int, ms_per_step: float) -> float:
     """Whole-job throughput of independent replicas (weak scaling): every rank
     shuffles its own n_per_rank elements per step."""
@@ -492,7 +531,7 @@ def main():
     if not args.no_e2e and not capacity:
         # pinned buffers on the GPU's own NUMA node: allocate from a thread bound to its CPUs
         numa = _bind_to_gpu_cpus(local)
-        hosts = [torch.empty(n, dtype=torch.int64, pin_memory=True) for _ in range(2)]
+        hosts, host_kind, regions = _pinned_host_buffers(n, 2)
         for h in hosts:
             h.copy_(x)
         devs = [x, torch.empty_like(x)]
@@ -528,8 +567,10 @@ def main():
                "d2h_bytes_per_step": n * w, "ms_per_step": e_ms,
                "how": "pinned host -> device, shuffle, -> host every step; steps pipelined over two buffers "
                       "(upload, shuffle, download streams); fill and drain inside the timed region",
-               "host_cpus": numa}
-        del hosts, devs
+               "host_cpus": numa, "host_buffers": host_kind}
+        del devs
+        _release_host_buffers(hosts, regions)
+        del hosts
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and not capacity:
