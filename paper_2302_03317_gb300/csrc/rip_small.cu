@@ -213,10 +213,9 @@ __device__ __forceinline__ void fy_draws_part(uint16_t* H, uint32_t len, PhiloxK
     }
 }
 
-// Children of a scattered range: leaves are finished right away, larger ones
-// are pushed for another scatter.  start(b) = first output index of bucket b.
 // Partner draws of the leaf children of a scattered range, by every thread (tpc = blockDim/k
 // threads per child), into the range's source array X (not read any more, or never read).
+// start(b) = first output index of bucket b.
 template <typename StartFn>
 __device__ void children_draws(uint16_t* X, uint32_t a, uint32_t len, uint32_t k, uint32_t L, const DevPlan& plan,
                                PhiloxKey key, uint64_t o_r, StartFn start) {
@@ -231,7 +230,9 @@ __device__ void children_draws(uint16_t* X, uint32_t a, uint32_t len, uint32_t k
     }
 }
 
-// draws_done: children_draws already ran (and a barrier followed).
+// Children of a scattered range: leaves are finished right away, larger ones are pushed for
+// another scatter.  start(b) = first output index of bucket b; draws_done: children_draws
+// already ran (and a barrier followed).
 template <typename StartFn>
 __device__ void finish_children(SmallShared& sh, uint16_t* P0, uint16_t* X, uint16_t* Y, uint32_t a, uint32_t len,
                                 uint32_t k, uint32_t L, uint32_t buf, const DevPlan& plan, PhiloxKey key,
