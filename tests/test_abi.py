@@ -68,6 +68,11 @@ def test_default_plan_and_workspace_size_on_host():
     assert rip.rip_shuffle_workspace_size(100, 4, bad) == 0
     nested_bad = rip.Plan(ks=[4, 4], Ts=[16, 16], Bs=[2, 4], base=4)  # B must divide the previous B
     assert rip.rip_shuffle_workspace_size(100, 4, nested_bad) == 0
+    # the permutation keeps two blocks per 8-lane group in shared memory: B * w up to 29 KiB
+    fits = rip.Plan(ks=[16], Ts=[1 << 16], Bs=[1024], base=4096)      # 16 KiB blocks of records
+    too_big = rip.Plan(ks=[16], Ts=[1 << 16], Bs=[2048], base=4096)   # 32 KiB
+    assert rip.rip_shuffle_workspace_size(1 << 20, 16, fits) > 0
+    assert rip.rip_shuffle_workspace_size(1 << 20, 16, too_big) == 0
 
 
 def test_capacity_plan_keeps_aux_below_one_percent_at_2pow34():
