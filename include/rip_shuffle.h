@@ -35,8 +35,14 @@
  *     consistency check) are recorded in a device status word; they are
  *     reported by rip_get_device_status() and by the next call that syncs.
  *   - n <= 1 is a no-op returning RIP_OK.
- *   - Not thread-safe per device when the library-managed workspace is used
- *     (ws == NULL): calls from several host threads must be serialised.
+ *   - Library-managed workspace (ws == NULL): one per device, shared by every
+ *     call that passes no workspace.  The library orders each such call after
+ *     the previous one on the device (an event recorded on the previous call's
+ *     stream), so calls on different streams do not overlap on the GPU and do
+ *     not race on it; a call that needs a larger workspace synchronises the
+ *     device and reallocates.  Callers that want shuffles to run concurrently
+ *     on several streams pass their own workspaces.  Calls from several host
+ *     threads on one device must still be serialised by the caller.
  */
 #ifndef RIP_SHUFFLE_H
 #define RIP_SHUFFLE_H
@@ -84,8 +90,9 @@ typedef struct {
 
 /* Fills *plan with the library's default plan for n elements of elem_bytes:
  * k = 256 (k = 64 below 128 MiB of data, the paper's rule in Sec. 5), base
- * 4096, B sized so k*B*elem_bytes = 128 KiB, the root tile chosen so that the
- * root has one tile per streaming multiprocessor; where level 1 runs in place
+ * 4096, B sized so k*B*elem_bytes = 128 KiB, the root cut into 152 tiles (one
+ * per SM on GB300; the plan depends on n and elem_bytes only, never on the
+ * device, so a seed gives the same output on every GPU); where level 1 runs in place
  * (root children above 32K elements) its tile is 4/5 of the expected child, so
  * every child has a long and a short tile (the short ones keep the SMs busy
  * while a wave's long ones run), else one tile per subproblem.  Returns
@@ -95,7 +102,7 @@ int rip_default_plan(uint64_t n, uint32_t elem_bytes, rip_plan *plan);
 /* Fills *plan with a plan for inputs that fill most of the device (the
  * in-place requirement of Sec. 3 at its largest): k = 1024 buckets over two
  * levels, then Fisher-Yates (max_levels 2, base 4096); root blocks of 1 KiB and
- * root tiles one per streaming multiprocessor; 32-element blocks and one tile
+ * the root cut into 152 tiles (independent of the device); 32-element blocks and one tile
  * per subproblem at level 1.  For 2^34 elements its workspace is 0.86% of a
  * 4-byte input and 0.63% of an 8-byte one; the root level's fixed part (tails
  * and blocks of 152 tiles x 1024 buckets) makes the fraction larger for
@@ -124,9 +131,12 @@ int rip_shuffle_ex(void *data, uint64_t n, uint32_t elem_bytes, uint64_t seed,
  * NULL: every array uses its own default plan (rip_default_plan(ns[i])), so an
  * array's result is the same alone and in any batch.  Arrays that share a plan
  * run together: one level-synchronous pass over all of them, the small ones on
- * one SM each; groups with different plans run one after another on `stream`.
- * ptrs and ns are HOST arrays of `count` entries; the arrays must not overlap.
- * ws as in rip_shuffle_ex (the workspace is the largest any group needs). */
+ * one SM each.  Groups with different plans run concurrently: each on one of
+ * eight auxiliary streams that belong to the caller's `stream` (forked from it
+ * and joined back into it, so the call is still ordered on `stream`), each on
+ * its own slice of the workspace; the workspace is the sum of the groups'
+ * slices (ask the *_workspace_size function).  ptrs and ns are HOST arrays of
+ * `count` entries; the arrays must not overlap.  ws as in rip_shuffle_ex. */
 size_t rip_shuffle_batched_workspace_size(const uint64_t *ns, uint32_t count, uint32_t elem_bytes,
                                           const rip_plan *plan);
 int rip_shuffle_batched(void *const *ptrs, const uint64_t *ns, uint32_t count, uint32_t elem_bytes,
@@ -165,6 +175,24 @@ int rip_get_device_status(rip_stream_t stream);
 
 /* Frees the library-managed workspace of the current device. */
 int rip_release_workspace(void);
+
+/* Testing hook for the allocation-failure path (Sec. 1 names failing
+ * allocations as a reason for in-place shuffling): the next `count` device
+ * allocations the library would make for its managed workspace fail as if
+ * cudaMalloc had failed, so the call returns RIP_ENOMEM before enqueuing any
+ * work (the data stay untouched).  count 0 turns it off. */
+int rip_debug_fail_allocations(uint32_t count);
+
+/* Testing hook for the bounded device-side waits: later calls give every
+ * hand-off wait of the classify step (input arrived, chunks read out, round
+ * placed) and every chain wait of the block permutation at most `polls`
+ * polls (the first one non-blocking) instead of the built-in limits (2^26
+ * mbarrier polls, 2^24 spins).  A wait that runs out records RIP_ETIMEOUT;
+ * the kernel finishes its own copies in flight and returns, the call's later
+ * kernels skip their work, and rip_get_device_status reports RIP_ETIMEOUT.
+ * The data of that call are then not a valid shuffle.  polls 0 restores the
+ * built-in limits. */
+int rip_debug_set_wait_limit(uint32_t polls);
 
 /* Static message for a return code. */
 const char *rip_strerror(int code);

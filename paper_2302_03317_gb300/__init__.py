@@ -118,6 +118,10 @@ def _load():
         lib.rip_get_device_status.restype = i32
         lib.rip_release_workspace.argtypes = []
         lib.rip_release_workspace.restype = i32
+        lib.rip_debug_fail_allocations.argtypes = [u32]
+        lib.rip_debug_fail_allocations.restype = i32
+        lib.rip_debug_set_wait_limit.argtypes = [u32]
+        lib.rip_debug_set_wait_limit.restype = i32
         lib.rip_strerror.argtypes = [i32]
         lib.rip_strerror.restype = ctypes.c_char_p
         lib.rip_last_call_info.argtypes = [ctypes.POINTER(u64)]
@@ -245,6 +249,16 @@ def rip_get_device_status(stream: int = 0) -> int:
 
 def rip_release_workspace() -> None:
     _check(_load().rip_release_workspace(), "rip_release_workspace")
+
+
+def rip_debug_fail_allocations(count: int) -> None:
+    """The next `count` managed-workspace allocations fail (tests of RIP_ENOMEM)."""
+    _check(_load().rip_debug_fail_allocations(count), "rip_debug_fail_allocations")
+
+
+def rip_debug_set_wait_limit(polls: int) -> None:
+    """Device-side wait limit for later calls (0: built-in limits; tests of RIP_ETIMEOUT)."""
+    _check(_load().rip_debug_set_wait_limit(polls), "rip_debug_set_wait_limit")
 
 
 def rip_strerror(code: int) -> str:

@@ -101,7 +101,7 @@ struct LevelCaps {
 
 struct Layout {
     size_t total = 0;
-    size_t arrays, lists_big0, lists_big1, small, medium, bigfy, counts, counters, pool_used;
+    size_t cstatus, arrays, lists_big0, lists_big1, small, medium, bigfy, counts, counters, pool_used;
     size_t tiles, sched, sp_tile_begin, segs, C, FBc, TLc, tinfo, child, words, pool, dem, parks, mscratch;
     uint32_t big_cap, small_cap, medium_cap, bigfy_cap, tile_cap, dem_cap, park_cap, levels, wave_cap;
     uint32_t medium_grid;
@@ -330,6 +330,7 @@ Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& 
         off = align_up(off + std::max<size_t>(bytes, 1), 256);
         return o;
     };
+    L.cstatus = take(sizeof(Status));
     L.arrays = take(sizeof(ArrayDesc) * narr);
     L.lists_big0 = take(sizeof(Sub) * L.big_cap);
     L.lists_big1 = take(sizeof(Sub) * L.big_cap);
@@ -365,19 +366,25 @@ Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& 
     return L;
 }
 
-bool default_plan_impl(uint64_t n, uint32_t w, rip_plan* p, uint32_t num_sms) {
+// Plans are a function of (n, w) alone: the root is always cut into kRootSplit tiles, whatever
+// GPU runs the call (152 is GB300's SM count, so there the root has one tile per SM).  The tile
+// split is part of the canonical output (Sec. 5: the result is reproducible from the seed);
+// the SM count of the device changes only the schedule, never (k, T, B).
+constexpr uint32_t kRootSplit = 152;
+
+bool default_plan_impl(uint64_t n, uint32_t w, rip_plan* p) {
     if (!valid_w(w) || !p) return false;
     std::memset(p, 0, sizeof(*p));
     const uint64_t bytes = n * w;
     const uint32_t k = bytes < (128ull << 20) ? 64 : 256;  // Sec. 5: k = 64 below 128 MiB, else 256
     uint32_t B = (uint32_t)((128u * 1024u) / (k * w));
     B = std::max<uint32_t>(1, std::min<uint32_t>(B, 1024));
-    // level 0: one tile per SM (rounded to a multiple of B); deeper levels: one tile per subproblem,
+    // level 0: kRootSplit tiles (rounded to a multiple of B); deeper levels: one tile per subproblem,
     // or, where level 1 runs in place, two: the first 4/5 of the expected subproblem and the rest.
     // Classify takes all first tiles before the short ones, so when a wave holds fewer
     // subproblems than SMs the idle SMs work through the short tiles meanwhile (measured on
     // GB300 at 2^30 u64, 128 subproblems per wave on 152 SMs: 4/5 best of 0.6 to 0.95)
-    uint64_t T0 = (n + num_sms - 1) / std::max<uint32_t>(num_sms, 1);
+    uint64_t T0 = (n + kRootSplit - 1) / kRootSplit;
     T0 = std::max<uint64_t>(T0, (uint64_t)B * 64);
     T0 = (T0 + B - 1) / B * B;
     T0 = std::min<uint64_t>(T0, (uint64_t)B << 20);
@@ -408,13 +415,13 @@ bool default_plan_impl(uint64_t n, uint32_t w, rip_plan* p, uint32_t num_sms) {
 // Plan for inputs that fill most of the device (the near-capacity case): k = 1024 buckets
 // over two levels, then Fisher-Yates; blocks of 1 KiB at the root (the slot table costs 4
 // bytes per block) and 32 elements below (the tails of the 2^20 deeper tiles cost about
-// B/2 elements each); root tiles one per SM, one tile per level-1 subproblem.
-bool capacity_plan_impl(uint64_t n, uint32_t w, rip_plan* p, uint32_t num_sms) {
+// B/2 elements each); kRootSplit root tiles, one tile per level-1 subproblem.
+bool capacity_plan_impl(uint64_t n, uint32_t w, rip_plan* p) {
     if (!valid_w(w) || !p) return false;
     std::memset(p, 0, sizeof(*p));
     const uint32_t k = 1024;
     const uint32_t B0 = 1024u / w, B1 = 32;
-    uint64_t T0 = (n + num_sms - 1) / std::max<uint32_t>(num_sms, 1);
+    uint64_t T0 = (n + kRootSplit - 1) / kRootSplit;
     T0 = std::max<uint64_t>(T0, (uint64_t)B0 * 64);
     T0 = (T0 + B0 - 1) / B0 * B0;
     T0 = std::min<uint64_t>(T0, (uint64_t)B0 << 20) / B0 * B0;
@@ -430,21 +437,47 @@ bool capacity_plan_impl(uint64_t n, uint32_t w, rip_plan* p, uint32_t num_sms) {
     return true;
 }
 
-constexpr uint32_t kAuxStreams = 8;  // plan groups of one batched call run concurrently on these
+constexpr uint32_t kAuxStreams = 8;   // plan groups of one batched call run concurrently on these
+constexpr uint32_t kAuxSets = 32;     // caller streams with their own auxiliary streams, per device
+
+// Auxiliary streams and fork/join events of one caller stream: batched calls issued on different
+// caller streams never share them, so their plan groups overlap on the device as the callers'
+// streams do, and calls from several host threads on different streams do not share events.
+struct AuxSet {
+    cudaStream_t caller = nullptr;
+    cudaStream_t aux[kAuxStreams] = {};
+    cudaEvent_t fork = nullptr, join[kAuxStreams] = {};
+    uint64_t last_use = 0;
+};
 
 struct DevState {
     void* ws = nullptr;
     size_t ws_bytes = 0;
+    cudaEvent_t ws_done = nullptr;  // recorded after the last call that used the managed workspace
+    bool ws_used = false;
     uint32_t num_sms = 0;
     Status* status = nullptr;
     unsigned long long* digest_buf = nullptr;
     uint64_t last_info[3] = {0, 0, 0};
-    cudaStream_t aux[kAuxStreams] = {};
-    cudaEvent_t fork = nullptr, join[kAuxStreams] = {};
+    std::vector<AuxSet*> aux_sets;
+    uint64_t aux_clock = 0;
 };
 
 std::mutex g_mutex;
 std::vector<DevState> g_dev;
+
+// Host-side fault injection for tests of the allocation-failure path (RIP_ENOMEM): while
+// g_fail_allocs > 0, every workspace allocation the library would make fails instead (and
+// decrements the counter).  Set through rip_test_fail_allocations.
+uint32_t g_fail_allocs = 0;
+// Limit of the device-side hand-off and chain waits (0: the built-in limits); set through
+// rip_debug_set_wait_limit to test the RIP_ETIMEOUT path.
+uint32_t g_wait_polls = 0;
+bool alloc_allowed() {
+    if (g_fail_allocs == 0) return true;
+    --g_fail_allocs;
+    return false;
+}
 
 DevState* dev_state(int* dev_out) {
     int dev = 0;
@@ -527,12 +560,13 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
 
     uint32_t* counters = reinterpret_cast<uint32_t*>(wsp + lay.counters);
     uint64_t* pool_used = reinterpret_cast<uint64_t*>(wsp + lay.pool_used);
+    Status* cst = reinterpret_cast<Status*>(wsp + lay.cstatus);  // this call's status word
     uint32_t launches = 0;
 
     ia.arrays = d_arr;
     ia.narrays = (uint32_t)arr.size();
     ia.plan = dplan;
-    ia.status = ds->status;
+    ia.status = cst;
     ia.lists = lists;
     ia.small_max_m = lay.small_max_m;
     ia.counters = counters;
@@ -544,10 +578,10 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
     ++launches;
 
     auto run_small = [&]() -> int {
-        SmallArgs sa{lists.small, lists.small_count, lists.small_cap, d_arr, dplan, ds->status, nullptr, 0, 0};
+        SmallArgs sa{lists.small, lists.small_count, lists.small_cap, d_arr, dplan, cst, nullptr, 0, 0};
         const size_t smem = small_smem_bytes(lay.small_max_m, w, false);
         if (launch_small(sa, w, smem, ds->num_sms, stream) != cudaSuccess) return RIP_ECUDA;
-        SmallArgs ma{lists.medium, lists.medium_count, lists.medium_cap, d_arr, dplan, ds->status,
+        SmallArgs ma{lists.medium, lists.medium_count, lists.medium_cap, d_arr, dplan, cst,
                      wsp + lay.mscratch, (uint64_t)kMediumMaxM * w, 1};
         const size_t msmem = small_smem_bytes(kMediumMaxM, w, true);
         if (launch_small(ma, w, msmem, lay.medium_grid, stream) != cudaSuccess) return RIP_ECUDA;
@@ -562,7 +596,8 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
         LevelArgs a{};
         a.arrays = d_arr;
         a.plan = dplan;
-        a.status = ds->status;
+        a.status = cst;
+        a.wait_polls = g_wait_polls;
         a.level = lev;
         a.k = plan.level[li].k;
         a.B = plan.level[li].block;
@@ -618,7 +653,7 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
         if (rc) return rc;
     }
     if (launch_bigfy(lists.bigfy, lists.bigfy_count, lists.bigfy_cap, d_arr, dplan, w,
-                     lists.big_count[lay.levels & 1], ds->status, stream) != cudaSuccess)
+                     lists.big_count[lay.levels & 1], cst, ds->status, stream) != cudaSuccess)
         return RIP_ECUDA;
     ++launches;
     ds->last_info[1] = std::max<uint64_t>(ds->last_info[1], lay.levels);
@@ -642,13 +677,13 @@ bool same_plan(const rip_plan& a, const rip_plan& b) {
 }
 
 std::vector<Group> group_arrays(const uint64_t* ns, uint32_t count, uint32_t w, const rip_plan* uniform,
-                                const rip_plan* plans, uint32_t num_sms) {
+                                const rip_plan* plans) {
     std::vector<Group> groups;
     for (uint32_t i = 0; i < count; ++i) {
         rip_plan p;
         if (uniform) p = *uniform;
         else if (plans) p = plans[i];
-        else default_plan_impl(ns[i], w, &p, num_sms);
+        else default_plan_impl(ns[i], w, &p);
         Group* g = nullptr;
         for (Group& x : groups)
             if (same_plan(x.plan, p)) {
@@ -679,9 +714,16 @@ size_t groups_workspace(const std::vector<Group>& groups, const uint64_t* ns, ui
     return need;
 }
 
-// The library-managed workspace of the current device, grown to `need` bytes.
-char* managed_workspace(DevState* ds, size_t need) {
+// The library-managed workspace of the current device, grown to `need` bytes.  The caller's
+// stream is ordered after the previous call that used it (on whatever stream), so calls with the
+// managed workspace never overlap on the device; callers that want concurrent shuffles pass
+// their own workspaces.
+char* managed_workspace(DevState* ds, size_t need, cudaStream_t stream) {
     std::lock_guard<std::mutex> lock(g_mutex);
+    if (!ds->ws_done && cudaEventCreateWithFlags(&ds->ws_done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
     if (ds->ws_bytes < need) {
         if (ds->ws) {
             cudaDeviceSynchronize();
@@ -689,23 +731,52 @@ char* managed_workspace(DevState* ds, size_t need) {
             ds->ws = nullptr;
             ds->ws_bytes = 0;
         }
-        if (cudaMalloc(&ds->ws, need) != cudaSuccess) {
+        if (!alloc_allowed() || cudaMalloc(&ds->ws, need) != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
         }
         ds->ws_bytes = need;
+        ds->ws_used = false;
+    } else if (ds->ws_used && cudaStreamWaitEvent(stream, ds->ws_done, 0) != cudaSuccess) {
+        return nullptr;
     }
     return static_cast<char*>(ds->ws);
 }
 
-bool aux_streams(DevState* ds) {
+// Marks the end of a call that used the managed workspace (on `stream`).
+bool managed_workspace_done(DevState* ds, cudaStream_t stream) {
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (ds->fork) return true;
-    for (uint32_t i = 0; i < kAuxStreams; ++i) {
-        if (cudaStreamCreateWithFlags(&ds->aux[i], cudaStreamNonBlocking) != cudaSuccess) return false;
-        if (cudaEventCreateWithFlags(&ds->join[i], cudaEventDisableTiming) != cudaSuccess) return false;
+    ds->ws_used = true;
+    return cudaEventRecord(ds->ws_done, stream) == cudaSuccess;
+}
+
+// The auxiliary set of `caller` (created on first use; the least recently used set is reused
+// for a new caller stream once kAuxSets exist -- that caller's earlier work is still ordered
+// before, because every batched call joins its auxiliary streams back into its caller).
+AuxSet* aux_set(DevState* ds, cudaStream_t caller) {
+    std::lock_guard<std::mutex> lock(g_mutex);
+    ++ds->aux_clock;
+    for (AuxSet* a : ds->aux_sets)
+        if (a->caller == caller) {
+            a->last_use = ds->aux_clock;
+            return a;
+        }
+    AuxSet* a = nullptr;
+    if (ds->aux_sets.size() < kAuxSets) {
+        a = new AuxSet();
+        for (uint32_t i = 0; i < kAuxStreams; ++i) {
+            if (cudaStreamCreateWithFlags(&a->aux[i], cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+            if (cudaEventCreateWithFlags(&a->join[i], cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        }
+        if (cudaEventCreateWithFlags(&a->fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        ds->aux_sets.push_back(a);
+    } else {
+        a = *std::min_element(ds->aux_sets.begin(), ds->aux_sets.end(),
+                              [](const AuxSet* x, const AuxSet* y) { return x->last_use < y->last_use; });
     }
-    return cudaEventCreateWithFlags(&ds->fork, cudaEventDisableTiming) == cudaSuccess;
+    a->caller = caller;
+    a->last_use = ds->aux_clock;
+    return a;
 }
 
 int run_groups(void* const* ptrs, const uint64_t* ns, uint32_t count, uint32_t w, uint64_t base_seed,
@@ -724,26 +795,30 @@ int run_groups(void* const* ptrs, const uint64_t* ns, uint32_t count, uint32_t w
     DevState* ds = dev_state(nullptr);
     if (!ds) return RIP_ECUDA;
     ds->last_info[0] = ds->last_info[1] = ds->last_info[2] = 0;
-    const std::vector<Group> groups = group_arrays(ns, count, w, uniform, plans, ds->num_sms);
+    const std::vector<Group> groups = group_arrays(ns, count, w, uniform, plans);
     for (const Group& g : groups)
         if (validate_plan(g.plan, w) != RIP_OK) return RIP_EINVAL;
     std::vector<size_t> offs;
     const size_t need = groups_workspace(groups, ns, w, &offs);
     char* wsp = static_cast<char*>(ws);
+    const bool managed = !wsp;
     if (wsp) {
         if (ws_bytes < need || (reinterpret_cast<uintptr_t>(wsp) & 255)) return RIP_EWORKSPACE;
     } else {
-        wsp = managed_workspace(ds, need);
+        wsp = managed_workspace(ds, need, stream);
         if (!wsp) return RIP_ENOMEM;
     }
     // one group runs on the caller's stream; several run concurrently, group g on auxiliary
-    // stream g mod 8 with its own workspace slice, forked from and joined into the stream
+    // stream g mod 8 of the caller stream's set, each group on its own workspace slice, forked
+    // from and joined into the caller's stream
     const bool fan = groups.size() > 1;
+    AuxSet* as = nullptr;
     if (fan) {
-        if (!aux_streams(ds)) return RIP_ECUDA;
-        if (cudaEventRecord(ds->fork, stream) != cudaSuccess) return RIP_ECUDA;
+        as = aux_set(ds, stream);
+        if (!as) return RIP_ECUDA;
+        if (cudaEventRecord(as->fork, stream) != cudaSuccess) return RIP_ECUDA;
         for (uint32_t a = 0; a < kAuxStreams && a < groups.size(); ++a)
-            if (cudaStreamWaitEvent(ds->aux[a], ds->fork, 0) != cudaSuccess) return RIP_ECUDA;
+            if (cudaStreamWaitEvent(as->aux[a], as->fork, 0) != cudaSuccess) return RIP_ECUDA;
     }
     int rc = RIP_OK;
     for (size_t gi = 0; gi < groups.size() && rc == RIP_OK; ++gi) {
@@ -756,15 +831,16 @@ int run_groups(void* const* ptrs, const uint64_t* ns, uint32_t count, uint32_t w
             n.push_back(ns[i]);
             seeds.push_back(seeds_in ? seeds_in[i] : base_seed + i);
         }
-        const cudaStream_t st = fan ? ds->aux[gi % kAuxStreams] : stream;
+        const cudaStream_t st = fan ? as->aux[gi % kAuxStreams] : stream;
         rc = run_shuffle(p, n, seeds, w, g.plan, wsp + offs[gi], need - offs[gi], st);
     }
     if (fan) {  // join even after an error, so the caller's stream orders everything enqueued
         for (uint32_t a = 0; a < kAuxStreams && a < groups.size(); ++a) {
-            if (cudaEventRecord(ds->join[a], ds->aux[a]) != cudaSuccess) return RIP_ECUDA;
-            if (cudaStreamWaitEvent(stream, ds->join[a], 0) != cudaSuccess) return RIP_ECUDA;
+            if (cudaEventRecord(as->join[a], as->aux[a]) != cudaSuccess) return RIP_ECUDA;
+            if (cudaStreamWaitEvent(stream, as->join[a], 0) != cudaSuccess) return RIP_ECUDA;
         }
     }
+    if (managed && !managed_workspace_done(ds, stream)) return RIP_ECUDA;
     return rc;
 }
 
@@ -777,14 +853,12 @@ extern "C" {
 
 int rip_default_plan(uint64_t n, uint32_t elem_bytes, rip_plan* plan) {
     if (!plan || !valid_w(elem_bytes)) return RIP_EINVAL;
-    DevState* ds = dev_state(nullptr);
-    return default_plan_impl(n, elem_bytes, plan, ds ? ds->num_sms : 152) ? RIP_OK : RIP_EINVAL;
+    return default_plan_impl(n, elem_bytes, plan) ? RIP_OK : RIP_EINVAL;
 }
 
 int rip_capacity_plan(uint64_t n, uint32_t elem_bytes, rip_plan* plan) {
     if (!plan || !valid_w(elem_bytes)) return RIP_EINVAL;
-    DevState* ds = dev_state(nullptr);
-    return capacity_plan_impl(n, elem_bytes, plan, ds ? ds->num_sms : 152) ? RIP_OK : RIP_EINVAL;
+    return capacity_plan_impl(n, elem_bytes, plan) ? RIP_OK : RIP_EINVAL;
 }
 
 size_t rip_shuffle_workspace_size(uint64_t n, uint32_t elem_bytes, const rip_plan* plan) {
@@ -795,25 +869,19 @@ size_t rip_shuffle_workspace_size(uint64_t n, uint32_t elem_bytes, const rip_pla
 size_t rip_shuffle_batched_workspace_size(const uint64_t* ns, uint32_t count, uint32_t elem_bytes,
                                           const rip_plan* plan) {
     if (!valid_w(elem_bytes) || (count && !ns)) return 0;
-    DevState* ds = dev_state(nullptr);
-    return groups_workspace(group_arrays(ns, count, elem_bytes, plan, nullptr, ds ? ds->num_sms : 152), ns,
-                            elem_bytes);
+    return groups_workspace(group_arrays(ns, count, elem_bytes, plan, nullptr), ns, elem_bytes);
 }
 
 size_t rip_shuffle_batched_ex_workspace_size(const uint64_t* ns, uint32_t count, uint32_t elem_bytes,
                                              const rip_plan* plans) {
     if (!valid_w(elem_bytes) || (count && !ns)) return 0;
-    DevState* ds = dev_state(nullptr);
-    return groups_workspace(group_arrays(ns, count, elem_bytes, nullptr, plans, ds ? ds->num_sms : 152), ns,
-                            elem_bytes);
+    return groups_workspace(group_arrays(ns, count, elem_bytes, nullptr, plans), ns, elem_bytes);
 }
 
 size_t rip_shuffle_batched_plans_workspace_size(const uint64_t* ns, uint32_t count, uint32_t elem_bytes,
                                                 const rip_plan* plans) {
     if (!valid_w(elem_bytes) || (count && (!ns || !plans))) return 0;
-    DevState* ds = dev_state(nullptr);
-    return groups_workspace(group_arrays(ns, count, elem_bytes, nullptr, plans, ds ? ds->num_sms : 152), ns,
-                            elem_bytes);
+    return groups_workspace(group_arrays(ns, count, elem_bytes, nullptr, plans), ns, elem_bytes);
 }
 
 int rip_shuffle(void* data, uint64_t n, uint32_t elem_bytes, uint64_t seed, rip_stream_t stream) {
@@ -892,7 +960,20 @@ int rip_release_workspace(void) {
         cudaFree(ds->ws);
         ds->ws = nullptr;
         ds->ws_bytes = 0;
+        ds->ws_used = false;
     }
+    return RIP_OK;
+}
+
+int rip_debug_fail_allocations(uint32_t count) {
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_fail_allocs = count;
+    return RIP_OK;
+}
+
+int rip_debug_set_wait_limit(uint32_t polls) {
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_wait_polls = polls;
     return RIP_OK;
 }
 

@@ -52,7 +52,9 @@ struct ClsMisc {
     uint32_t tile;
     uint32_t home_next;
     uint32_t nflush[2];
-    uint32_t fail;
+    uint32_t fail;   // a wait of this CTA expired (either role)
+    uint32_t cfail;  // the compute warps' verdict for the current round (written by thread 0 before
+                     // a compute barrier, read by every compute thread after it)
     uint32_t scan[32];
 };
 
@@ -135,6 +137,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
     const uint32_t b_shift = log2_pow2(B);
     const bool flush_vec = a.vec16 && (Bs * W) % 16u == 0;
     T* pool = reinterpret_cast<T*>(a.pool);
+    const uint32_t polls = a.wait_polls ? a.wait_polls : kMbarPolls;  // hand-off waits
 
     for (uint32_t j = tid; j < nwr * 32u; j += blockDim.x) masks[j] = 0;  // kept zero after every step
     if (tid == 0) {
@@ -152,7 +155,8 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
     for (;;) {
         if (tid == 0) {
             const uint32_t c = atomicAdd(&a.counters[1], 1u);
-            ms.tile = c < ntiles ? a.sched[c] : c;
+            ms.tile = c < ntiles && !call_failed(a.status) ? a.sched[c] : 0xffffffffu;
+            ms.cfail = 0;
         }
         __syncthreads();
         const uint32_t tile = ms.tile;
@@ -206,6 +210,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
         };
         uint32_t carried[4] = {kNone, kNone, kNone, kNone};
         uint32_t carried_buf = 0;  // buffer of the carried elements
+        uint32_t loads_issued = 0;  // I/O warp: rounds whose load has been issued
 
         if (io) {
             // ---------------------------------------------------------------- I/O warp
@@ -213,6 +218,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
             // the lanes copy ragged ends and the rotation's wrap piece
             auto load = [&](uint32_t rr) {
                 const uint32_t gr = grc + rr;
+                loads_issued = rr + 1u;
                 T* buf = bufs + (size_t)(gr % nbuf) * g.bufstride;
                 const uint32_t R = rr * round;
                 const uint32_t sh = shift_of(rr);
@@ -248,15 +254,20 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
             if (lane == 0) mbar_arrive(&ms.stage_free);  // round 0 may place: nothing to flush yet
             for (uint32_t rr = 0; rr < nrounds; ++rr) {
                 // round rr is placed: its chunks and flush list are ready, the buffer of rr-1 is free
+                // (lane 0 decides for the warp: its wait, or a failure the compute warps recorded)
                 uint32_t ok = 1;
-                if (lane == 0) ok = mbar_wait(&ms.flush_ready, (frc + rr) & 1u);
+                if (lane == 0) {
+                    ok = mbar_wait(&ms.flush_ready, (frc + rr) & 1u, polls);
+                    if (!ok) {
+                        report(a.status, RIP_ETIMEOUT, 0x6208, rr);
+                        ms.fail = 1;
+                    } else if (ms.fail) {
+                        ok = 0;
+                    }
+                }
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 __syncwarp();  // lane 0's acquire covers the whole warp
-                if (!ok) {
-                    if (lane == 0) report(a.status, RIP_ETIMEOUT, 0x6208, rr);
-                    ms.fail = 1;
-                }
-                if (!ok || ms.fail) break;
+                if (!ok) break;
                 if (rr + nbuf - 1 < nrounds) load(rr + nbuf - 1);
                 const uint32_t par = rr & 1u;
                 const uint32_t nf = ms.nflush[par];
@@ -294,6 +305,16 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&ms.stage_free);  // the chunks are read out: round rr+1 may place
             }
+            // after a failure: the loads still in flight land in this CTA's shared memory, so they
+            // complete before the CTA leaves (the last load of each buffer; earlier ones were
+            // consumed); stores issued by this warp have read their sources already
+            if (ms.fail && lane == 0) {
+                for (uint32_t j = loads_issued > nbuf ? loads_issued - nbuf : 0u; j < loads_issued; ++j) {
+                    const uint32_t gr = grc + j;
+                    mbar_wait(&ms.full[gr % nbuf], (gr / nbuf) & 1u);
+                }
+            }
+            __syncwarp();
         } else {
             // ---------------------------------------------------------------- compute warps
             for (uint32_t rr = 0; rr < nrounds; ++rr) {
@@ -471,17 +492,17 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                 }
                 // this round's input is loaded and the previous round's chunks are read out
                 if (tid == 0) {
-                    if (!mbar_wait(&ms.full[gr % nbuf], (gr / nbuf) & 1u)) {
+                    if (!mbar_wait(&ms.full[gr % nbuf], (gr / nbuf) & 1u, polls)) {
                         report(a.status, RIP_ETIMEOUT, 0x6207, gr);
                         ms.fail = 1;
-                    }
-                    if (!mbar_wait(&ms.stage_free, (sfc + rr) & 1u)) {
+                    } else if (!mbar_wait(&ms.stage_free, (sfc + rr) & 1u, polls)) {
                         report(a.status, RIP_ETIMEOUT, 0x6209, gr);
                         ms.fail = 1;
                     }
+                    ms.cfail = ms.fail;  // one verdict for all compute warps (ms.fail may change later)
                 }
                 compute_sync();  // B
-                if (ms.fail) {
+                if (ms.cfail) {
                     if (tid == 0) mbar_arrive(&ms.flush_ready);  // lets the I/O warp see the failure
                     break;
                 }
@@ -543,8 +564,9 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                 if (tid == 0) mbar_arrive(&ms.flush_ready);
             }
             // end of the tile: the last chunks are read out, then the carried elements
-            if (!ms.fail) {
-                if (tid == 0 && !mbar_wait(&ms.stage_free, (sfc + nrounds) & 1u)) {
+            // (ms.cfail is the verdict every compute thread saw at the last barrier B)
+            if (!ms.cfail) {
+                if (tid == 0 && !mbar_wait(&ms.stage_free, (sfc + nrounds) & 1u, polls)) {
                     report(a.status, RIP_ETIMEOUT, 0x620A, nrounds);
                     ms.fail = 1;
                 }

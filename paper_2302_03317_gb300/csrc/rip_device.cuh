@@ -42,6 +42,25 @@ __device__ __forceinline__ void report(Status* st, uint32_t code, uint32_t where
     }
 }
 
+// Every call has its own status word (in its workspace).  Once a kernel of the call has
+// recorded an error, the call's later kernels skip their work: their inputs (counts, slot
+// words, lists) may be incomplete.  The call's last kernel copies the word into the
+// device's status word, which rip_get_device_status returns.
+__device__ __forceinline__ bool call_failed(const Status* st) {
+    return *reinterpret_cast<const volatile uint32_t*>(&st->code) != 0u;
+}
+
+// The same verdict for every thread of the block (read once by thread 0); call it from every
+// thread at the start of a kernel.
+__device__ __forceinline__ bool block_call_failed(const Status* st) {
+    __shared__ uint32_t failed;
+    if (threadIdx.x == 0) failed = call_failed(st) ? 1u : 0u;
+    __syncthreads();
+    const bool r = failed != 0u;
+    __syncthreads();
+    return r;
+}
+
 // ----------------------------------------------------------------- Philox
 
 struct PhiloxKey {
@@ -314,11 +333,18 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-// Bounded wait for the phase with the given parity; false after kMbarPolls polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait for the phase with the given parity: one non-blocking test, then up to
+// polls - 1 potentially blocking tries; false when the phase has not completed by then.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t polls = kMbarPolls) {
     const uint32_t a = smem_addr(bar);
-    for (uint32_t i = 0; i < kMbarPolls; ++i) {
-        uint32_t done;
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    for (uint32_t i = 1; i < polls; ++i) {
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)

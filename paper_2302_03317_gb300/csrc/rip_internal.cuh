@@ -145,6 +145,7 @@ struct LevelArgs {
     ParkRec* parks;
     uint32_t park_cap;
     uint32_t park_after;  // chain steps before a carried block is parked
+    uint32_t wait_polls;  // limit of the hand-off and chain waits (0: the built-in limits)
     ClsCfg cls;
 };
 
@@ -199,8 +200,11 @@ size_t permute_smem_bytes(uint32_t B, uint32_t w);
 uint32_t permute_threads(uint32_t B, uint32_t w);
 cudaError_t launch_init(const InitArgs& a, cudaStream_t s);
 cudaError_t launch_level(const LevelArgs& a, uint32_t w, uint32_t num_sms, cudaStream_t s, uint32_t* launches);
+// The call's last kernel: copies the call's status word into the device's (global) one, then
+// finishes leaves too large for one SM.
 cudaError_t launch_bigfy(const Sub* list, const uint32_t* count, uint32_t cap, const ArrayDesc* arrays,
-                         DevPlan plan, uint32_t w, const uint32_t* leftover, Status* status, cudaStream_t s);
+                         DevPlan plan, uint32_t w, const uint32_t* leftover, Status* status, Status* global,
+                         cudaStream_t s);
 
 // rip_digest.cu
 cudaError_t launch_digest(const void* data, uint64_t n, uint32_t w, unsigned long long* out, cudaStream_t s);

@@ -90,6 +90,7 @@ __device__ void route_sub(const Sub& c, const DevPlan& plan, uint32_t small_max_
 __global__ void init_kernel(InitArgs a) {
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     if (tid == 0) {
+        *a.status = Status{};  // this call's status word starts clean
         *a.lists.big_count[0] = 0;
         *a.lists.big_count[1] = 0;
         *a.lists.small_count = 0;
@@ -116,8 +117,9 @@ __global__ void tiles_kernel(LevelArgs a) {
     __shared__ uint64_t scan64[32];
     __shared__ uint32_t carry;
     __shared__ uint64_t scarry;
+    const bool failed = block_call_failed(a.status);  // an earlier kernel failed: an empty wave
     const uint32_t nbig = min(*a.big_count, a.big_cap);
-    const uint32_t we = nbig > a.wb ? min(nbig - a.wb, a.wcap) : 0u;  // subproblems of this wave
+    const uint32_t we = nbig > a.wb && !failed ? min(nbig - a.wb, a.wcap) : 0u;  // subproblems of this wave
     const uint64_t B = a.B;
     if (threadIdx.x == 0) {
         carry = 0;
@@ -196,6 +198,7 @@ __global__ void tiles_kernel(LevelArgs a) {
 __global__ void scan_kernel(LevelArgs a, uint32_t small_max_m) {
     __shared__ uint64_t start[kMaxK];
     __shared__ uint64_t scan64[32];
+    if (block_call_failed(a.status)) return;
     const uint32_t k = a.k, B = a.B;
     const uint32_t we = a.counters[7];
     for (uint32_t wi = blockIdx.x; wi < we; wi += gridDim.x) {
@@ -258,6 +261,7 @@ __global__ void scan_kernel(LevelArgs a, uint32_t small_max_m) {
 // ------------------------------------------------------------------ resolve
 
 __global__ void resolve_kernel(LevelArgs a) {
+    if (block_call_failed(a.status)) return;
     const uint32_t ntiles = a.counters[0];
     const uint32_t k = a.k, B = a.B;
     for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -318,8 +322,8 @@ __global__ void __launch_bounds__(kPermuteThreads, 4) permute_kernel(LevelArgs a
     for (;;) {
         if (!carrying) {
             if (cpos >= 64) {
-                uint64_t c0 = 0;
-                if (leader) c0 = atomicAdd((unsigned long long*)&a.counters[4], 1ull);
+                uint64_t c0 = ~0ull;  // stays past the end once the call has failed
+                if (leader && !call_failed(a.status)) c0 = atomicAdd((unsigned long long*)&a.counters[4], 1ull);
                 chunk = __shfl_sync(gmask, c0, leader_lane);
                 if (chunk >= a.counters[8]) break;
                 const uint64_t s0 = chunk * 64u + lg * 8u;
@@ -444,10 +448,11 @@ __global__ void __launch_bounds__(kPermuteThreads, 4) permute_kernel(LevelArgs a
         __syncwarp(gmask);  // order the group's accesses to d after the leader's acquire
         if (old & kWordTaken) {
             // a chain start holds the slot: wait (bounded) until it has read it out
+            const uint32_t limit = a.wait_polls ? a.wait_polls : (1u << 24);
             uint32_t spins = 0;
             if (leader) {
                 while (ld_acquire(&a.words[d]) != 0u) {
-                    if (++spins > (1u << 24)) {
+                    if (++spins > limit) {
                         report(a.status, RIP_ETIMEOUT, 0x6401, d);
                         break;
                     }
@@ -456,7 +461,7 @@ __global__ void __launch_bounds__(kPermuteThreads, 4) permute_kernel(LevelArgs a
             }
             spins = __shfl_sync(gmask, spins, leader_lane);
             cp_async_wait_all();  // the incoming slot is reloaded on the next try
-            if (spins > (1u << 24)) {
+            if (spins > limit) {
                 carrying = false;  // give up; the error is reported
                 continue;
             }
@@ -486,6 +491,7 @@ __global__ void tails_kernel(LevelArgs a) {
     using T = typename Elem<W>::T;
     __shared__ uint32_t pre[kMaxK];
     __shared__ uint32_t scan[32];
+    if (block_call_failed(a.status)) return;
     const uint32_t ntiles = a.counters[0];
     const uint32_t k = a.k, B = a.B;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -528,6 +534,7 @@ __global__ void tails_kernel(LevelArgs a) {
 // the permutation kernel.
 template <typename U>
 __global__ void parked_kernel(LevelArgs a, uint32_t w) {
+    if (call_failed(a.status)) return;
     const uint32_t n = min(a.counters[6], a.park_cap);
     const uint32_t units = a.B * w / (uint32_t)sizeof(U);
     const uint32_t lane = threadIdx.x & 31u;
@@ -545,6 +552,7 @@ __global__ void parked_kernel(LevelArgs a, uint32_t w) {
 template <int W>
 __global__ void demoted_kernel(LevelArgs a) {
     using T = typename Elem<W>::T;
+    if (call_failed(a.status)) return;
     const uint32_t ndem = min(a.counters[2], a.dem_cap);
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -575,8 +583,12 @@ __global__ void demoted_kernel(LevelArgs a) {
 // sequential Fisher-Yates in global memory, one thread per leaf.
 template <int W>
 __global__ void bigfy_kernel(const Sub* list, const uint32_t* count, uint32_t cap, const ArrayDesc* arrays,
-                             DevPlan plan, const uint32_t* leftover, Status* status) {
+                             DevPlan plan, const uint32_t* leftover, Status* call, Status* status) {
     using T = typename Elem<W>::T;
+    // every earlier kernel of the call is complete: its status goes to the device's word
+    const Status cs = *call;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && cs.code) report(status, cs.code, cs.where, cs.detail);
+    if (cs.code) return;
     const uint32_t n = min(*count, cap);
     if (blockIdx.x == 0 && threadIdx.x == 0 && *leftover != 0)  // deeper recursion than the host planned
         report(status, RIP_EWORKSPACE, 0x6501, *leftover);
@@ -699,12 +711,13 @@ cudaError_t launch_level(const LevelArgs& a, uint32_t w, uint32_t num_sms, cudaS
 }
 
 cudaError_t launch_bigfy(const Sub* list, const uint32_t* count, uint32_t cap, const ArrayDesc* arrays,
-                         DevPlan plan, uint32_t w, const uint32_t* leftover, Status* status, cudaStream_t s) {
+                         DevPlan plan, uint32_t w, const uint32_t* leftover, Status* status, Status* global,
+                         cudaStream_t s) {
     ProfScope p("bigfy", s);
     switch (w) {
-        case 4: bigfy_kernel<4><<<8, 32, 0, s>>>(list, count, cap, arrays, plan, leftover, status); break;
-        case 8: bigfy_kernel<8><<<8, 32, 0, s>>>(list, count, cap, arrays, plan, leftover, status); break;
-        default: bigfy_kernel<16><<<8, 32, 0, s>>>(list, count, cap, arrays, plan, leftover, status); break;
+        case 4: bigfy_kernel<4><<<8, 32, 0, s>>>(list, count, cap, arrays, plan, leftover, status, global); break;
+        case 8: bigfy_kernel<8><<<8, 32, 0, s>>>(list, count, cap, arrays, plan, leftover, status, global); break;
+        default: bigfy_kernel<16><<<8, 32, 0, s>>>(list, count, cap, arrays, plan, leftover, status, global); break;
     }
     return cudaGetLastError();
 }

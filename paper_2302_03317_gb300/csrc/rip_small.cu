@@ -585,6 +585,7 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(SmallArgs args) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmallShared& sh = *reinterpret_cast<SmallShared*>(smem_raw);
     unsigned char* dyn = smem_raw + ((sizeof(SmallShared) + 15) & ~size_t(15));
+    if (block_call_failed(args.status)) return;  // an earlier kernel of the call failed
     const uint32_t count = min(*args.count, args.capacity);
     const uint32_t tid = threadIdx.x;
     const DevPlan& plan = args.plan;

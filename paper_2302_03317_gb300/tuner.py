@@ -4,8 +4,9 @@ Size class c holds the arrays with 2^c <= n < 2^(c+1).  For every class the tune
 batch of arrays of that class (sizes log-uniform inside it), times every candidate plan on it
 with rip_shuffle_batched_plans and CUDA events on the current stream, and keeps the fastest.
 Candidates vary the bucket count k (powers of two from 8 to 256), the block B (k B w = 32, 64
-or 128 KiB of staged buffers) and, through B, the root tile (one tile per SM, at least 64
-blocks); the base case stays 4096, the value of Sec. 5.
+or 128 KiB of staged buffers) and, through B, the root tile (the root cut into ROOT_SPLIT = 152
+tiles -- GB300's SM count -- of at least 64 blocks, whatever device runs the tuner, so a plan
+never depends on the GPU); the base case stays 4096, the value of Sec. 5.
 
 The table is plain data (JSON).  An array's output is a function of (seed, n, plan), so any
 reader of the table -- the oracle included -- reproduces the same result; an array's plan
@@ -25,6 +26,7 @@ from . import Plan, rip_default_plan, rip_get_device_status, rip_strerror
 
 CLASS_LO, CLASS_HI = 8, 20
 BASE = 4096
+ROOT_SPLIT = 152  # root tiles of every candidate, independent of the device (as in the library's plans)
 TUNED_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned")
 
 
@@ -32,13 +34,13 @@ def size_class(n: int) -> int:
     return max(0, int(n).bit_length() - 1)
 
 
-def candidate_plans(c: int, w: int, num_sms: int) -> List[Plan]:
+def candidate_plans(c: int, w: int) -> List[Plan]:
     n_hi = 1 << (c + 1)
     out = []
     for k in (8, 16, 32, 64, 128, 256):
         for staged in (32 << 10, 64 << 10, 128 << 10):
             B = max(1, min(1024, staged // (k * w)))
-            T0 = max(-(-n_hi // num_sms), B * 64)
+            T0 = max(-(-n_hi // ROOT_SPLIT), B * 64)
             T0 = min(-(-T0 // B) * B, B << 20)
             T1 = B << 20
             p = Plan(ks=[k, k], Ts=[T0, T1], Bs=[B, B], base=BASE, max_levels=0)
@@ -63,7 +65,6 @@ def tune(elem_bytes: int, classes: Sequence[int] = tuple(range(CLASS_LO, CLASS_H
     from . import shuffle_batched_
     w = elem_bytes
     dt = {4: torch.int32, 8: torch.int64}[w]
-    num_sms = torch.cuda.get_device_properties(0).multi_processor_count
     stream = torch.cuda.current_stream()
     rng = np.random.default_rng(seed)
     table = {"elem_bytes": w, "device": torch.cuda.get_device_name(0), "base": BASE, "classes": {}, "timings": {}}
@@ -76,7 +77,7 @@ def tune(elem_bytes: int, classes: Sequence[int] = tuple(range(CLASS_LO, CLASS_H
             o += (n + 3) // 4 * 4
         results = []
         default = rip_default_plan(1 << c, w)
-        for p in [default] + candidate_plans(c, w, num_sms):
+        for p in [default] + candidate_plans(c, w):
             plans = [p] * len(views)
             try:
                 for r in range(2):

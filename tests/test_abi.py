@@ -97,3 +97,44 @@ def test_oracle_and_library_share_no_code():
     assert "import oracle" not in pkg and "from oracle" not in pkg
     orc = open(os.path.join(ROOT, "oracle", "rip_oracle.c")).read()
     assert "#include \"" not in orc
+
+
+def _documented_default_plan(n, w):
+    """The default plan restated from its documentation in include/rip_shuffle.h: a function of
+    (n, w) alone -- k = 64 below 128 MiB of data, else 256; k * B * w = 128 KiB; the root cut into
+    152 tiles (a multiple of B, at least 64 blocks); level 1: where the root's children exceed 32K
+    elements, k1 the smallest power of two >= 16 leaving about 8K elements per child (at most
+    256) and a tile of 4/5 of the expected child, else the root's k and one tile per subproblem."""
+    k = 64 if n * w < (128 << 20) else 256
+    B = max(1, min(1024, (128 * 1024) // (k * w)))
+    T0 = max(-(-n // 152), B * 64)
+    T0 = min(-(-T0 // B) * B, B << 20) // B * B
+    m1 = n // k
+    k1, T1 = k, (B << 20) // B * B
+    if m1 > 32768:
+        k1 = 16
+        while k1 < 256 and k1 * 8192 < m1:
+            k1 *= 2
+        T1 = max(B * 64, -(-(4 * m1 // 5) // B) * B)
+    return [k, k1], [T0, T1], [B, B]
+
+
+@pytest.mark.parametrize("w", [4, 8, 16])
+def test_default_plan_depends_on_size_and_width_only(w):
+    """The plan (and so the canonical output, Sec. 5) is the documented function of (n, w): no
+    device attribute enters it.  The GPU tests check the same plans with a device visible."""
+    for e in (10, 16, 20, 22, 24, 26, 28, 30, 33, 34):
+        for n in (1 << e, (1 << e) + 12345, 3 << (e - 2)):
+            p = rip.rip_default_plan(n, w)
+            ks, Ts, Bs = _documented_default_plan(n, w)
+            assert (list(p.ks), list(p.Ts), list(p.Bs), p.base, p.max_levels) == (ks, Ts, Bs, 4096, 0), (n, w)
+            c = rip.rip_capacity_plan(n, w)
+            T0 = max(-(-n // 152), (1024 // w) * 64)
+            T0 = min(-(-T0 // (1024 // w)) * (1024 // w), (1024 // w) << 20) // (1024 // w) * (1024 // w)
+            assert list(c.Ts) == [T0, 32 << 20] and list(c.Bs) == [1024 // w, 32], (n, w)
+
+
+def test_allocation_failure_hook_and_wait_limit_hook_exist():
+    """The testing hooks of the failure paths are plain host setters (no device needed)."""
+    rip.rip_debug_fail_allocations(0)
+    rip.rip_debug_set_wait_limit(0)

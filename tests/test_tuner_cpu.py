@@ -20,7 +20,7 @@ def test_size_class_is_floor_log2():
 def test_every_candidate_is_a_valid_plan():
     for c in range(tuner.CLASS_LO, tuner.CLASS_HI + 1):
         for w in (4, 8):
-            cands = tuner.candidate_plans(c, w, 152)
+            cands = tuner.candidate_plans(c, w)
             assert cands, c
             keys = {(tuple(p.ks), tuple(p.Ts), tuple(p.Bs)) for p in cands}
             assert len(keys) == len(cands)  # no duplicates
