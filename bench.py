@@ -192,33 +192,55 @@ def job_rate(world_size: int, n_per_rank: int, ms_per_step: float) -> float:
     return world_size * n_per_rank / (ms_per_step / 1e3)
 
 
-def cpu_oracle_sample(plan, log2n: int):
-    """Times the CPU oracle (single thread, as it stands) on 2^log2n u64 iota."""
+# The library's default plan for 2^30 u64 elements (rip_default_plan(2^30, 8)), written out so
+# that the reference arm -- the CPU oracle -- runs without loading the CUDA library;
+# tests/test_bench_cpu.py checks that it equals the library's plan.
+DEFAULT_PLAN_2POW30_U64 = {"ks": [256, 256], "Ts": [7064128, 3355456], "Bs": [64, 64], "base": 4096,
+                           "max_levels": 0}
+
+
+def _host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_oracle_sample(plan, log2n: int, threads: int = 1):
+    """Times the CPU oracle as it stands on 2^log2n u64 iota: one thread (oracle.shuffle) or
+    `threads` host threads (oracle.shuffle_parallel: the root level, then the root's children
+    concurrently).  Returns (elements/s, seconds, n, output)."""
     import numpy as np
 
     import oracle
     n = 1 << log2n
     a = np.arange(n, dtype=np.uint64)
-    op = oracle.Plan(list(plan.ks), list(plan.Ts), list(plan.Bs), plan.base, plan.max_levels)
+    op = oracle.Plan(list(plan["ks"]), list(plan["Ts"]), list(plan["Bs"]), plan["base"], plan["max_levels"])
     t0 = time.perf_counter()
-    oracle.shuffle(a, SEED, op, inplace=True)
+    if threads > 1:
+        oracle.shuffle_parallel(a, SEED, op, threads=threads)
+    else:
+        oracle.shuffle(a, SEED, op, inplace=True)
     dt = time.perf_counter() - t0
-    return n / dt, dt, n
+    return n / dt, dt, n, a
+
+
+def _plan_dict(p):
+    return {"ks": list(p.ks), "Ts": list(p.Ts), "Bs": list(p.Bs), "base": p.base, "max_levels": p.max_levels}
 
 
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    import paper_2302_03317_gb300 as rip
-    n = 1 << N_LOG2
-    plan = rip.rip_default_plan(n, ELEM_BYTES)
+    plan = DEFAULT_PLAN_2POW30_U64  # the CUDA library is not loaded on this arm
     sample_log2 = args.ref_sample_log2
+    cores = _host_cores()
     for _ in range(args.warmup):
-        cpu_oracle_sample(plan, min(sample_log2, 18))
+        cpu_oracle_sample(plan, min(sample_log2, 18), threads=cores)
     times = []
     for _ in range(args.steps):
-        _, dt, ns = cpu_oracle_sample(plan, sample_log2)
+        _, dt, ns, _ = cpu_oracle_sample(plan, sample_log2, threads=cores)
         times.append(dt)
     rate = ns * len(times) / sum(times)
     line = {
@@ -226,19 +248,22 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": f"in-place shuffle of 2^{N_LOG2} u64 iota (default plan, seed {SEED}); "
-                               f"each step the CPU oracle on a 2^{sample_log2} sample with the same plan",
+                               f"each step the CPU oracle on a 2^{sample_log2} sample with the same plan "
+                               f"on {cores} host threads",
                    "sample_elems": ns},
-        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"2^{sample_log2} u64 iota, same plan, single thread"},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"2^{sample_log2} u64 iota, same plan, the oracle's threaded driver on "
+                                   f"{cores} host threads (root level on one, its children on all)"},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_batched(args, rip, torch, dist, ws, rank, local, barrier):
-    """Many independent shuffles: one rip_shuffle_batched call per step (each array its own
-    default plan) against one rip_shuffle call per array; same seeds, same results."""
+def measure_batched(args, rip, torch, dist, ws, barrier, steps, warmup):
+    """Many independent shuffles: one rip_shuffle_batched call per step (each array the plan
+    of its size class from the tuner's table, else its own default plan) against one rip_shuffle
+    call per array with the same plans, seeds and results.  Returns the measured figures."""
     from paper_2302_03317_gb300.inputs import batched_sizes
     sizes = [int(v) for v in batched_sizes(args.arrays, seed=SEED)]
     offs, o = [], 0
@@ -265,22 +290,19 @@ def run_batched(args, rip, torch, dist, ws, rank, local, barrier):
         for i, v in enumerate(views):
             rip.shuffle_(v, seed + i, plan=plans[i] if plans else None)
 
-    for i in range(args.warmup):
+    for i in range(warmup):
         batched(SEED + i)
     plain(SEED)
     rc = rip.rip_get_device_status(stream.cuda_stream)
     if rc != 0:
-        raise SystemExit(f"device status after warm-up: {rip.rip_strerror(rc)}")
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
+        raise SystemExit(f"device status after batched warm-up: {rip.rip_strerror(rc)}")
     rip.rip_profile_reset()
     rip.rip_profile_enable(True)
     torch.cuda.synchronize()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for i in range(args.steps):
+    for i in range(steps):
         batched(SEED + 100 * (i + 1))
     e1.record(stream)
     torch.cuda.synchronize()
@@ -288,43 +310,55 @@ def run_batched(args, rip, torch, dist, ws, rank, local, barrier):
     rip.rip_profile_enable(False)
     prof = rip.rip_profile_get()
     launches = sum(v[0] for v in prof.values())
-    ms_b = max_over_ranks(e0.elapsed_time(e1), dist, "cuda") / args.steps
+    ms_b = max_over_ranks(e0.elapsed_time(e1), dist, "cuda") / steps
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     p0.record(stream)
     plain(SEED + 7)
     p1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    clk = clocks.stop()
     ms_p = max_over_ranks(p0.elapsed_time(p1), dist, "cuda")
     rc = rip.rip_get_device_status(stream.cuda_stream)
     if rc != 0:
-        raise SystemExit(f"device status after timed steps: {rip.rip_strerror(rc)}")
+        raise SystemExit(f"device status after batched steps: {rip.rip_strerror(rc)}")
+    del buf, views
     value = job_rate(ws, total, ms_b)
     plain_rate = job_rate(ws, total, ms_p)
+    return {"value": value, "unit": UNIT, "ms_per_step": ms_b, "steps": steps, "arrays": args.arrays,
+            "elements": total, "elem_bytes": 4,
+            "workload": f"{args.arrays} u32 iota arrays, sizes log-uniform in [2^8, 2^20] "
+                        f"(numpy default_rng({SEED})), seed base_seed + i, "
+                        + ("tuned plan per size class" if plans else "default plan per array"),
+            "plain": {"value": plain_rate, "unit": UNIT, "ms_per_step": ms_p,
+                      "how": "one rip_shuffle call per array, same plans, seeds and results"},
+            "vs_plain": value / plain_rate,
+            "kernels": {k: {"launches": v[0], "ms_per_step": v[1] / steps} for k, v in sorted(prof.items())},
+            "gpu_launches": launches}
+
+
+def run_batched(args, rip, torch, dist, ws, rank, local, barrier):
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    m = measure_batched(args, rip, torch, dist, ws, barrier, args.steps, args.warmup)
+    clk = clocks.stop()
     hbm_gbs, peak_kind = _measured_hbm_gbs()
+    total, ms_b = m["elements"], m["ms_per_step"]
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": f"batched: {args.arrays} u32 iota arrays, sizes log-uniform in [2^8, 2^20] "
-                                   f"(numpy default_rng({SEED})), seed base_seed + i, "
-                                   + ("tuned plan per size class" if plans else "default plan per array"),
-                       "arrays": args.arrays, "elements": total, "elem_bytes": 4,
-                       "l2": f"{total * 4 / 2**30:.1f} GiB of arrays vs 129 MB L2",
+            "config": {"workload": "batched: " + m["workload"], "arrays": args.arrays, "elements": total,
+                       "elem_bytes": 4, "l2": f"{total * 4 / 2**30:.1f} GiB of arrays vs 129 MB L2",
                        "parallelism": f"replicas{ws}" if ws > 1 else "single"},
-            "plain": {"value": plain_rate, "unit": UNIT, "ms_per_step": ms_p,
-                      "how": "one rip_shuffle call per array, same seeds and results"},
-            "vs_plain": value / plain_rate,
+            "plain": m["plain"], "vs_plain": m["vs_plain"],
             "roofline": {"bound": "hbm", "kernel": "whole batched call", "achieved": 2 * 4 * total / (ms_b / 1e3) / 1e9,
                          "peak": hbm_gbs, "unit": "GB/s",
                          "frac": 2 * 4 * total / (ms_b / 1e3) / 1e9 / hbm_gbs, "traffic": None,
                          "peak_kind": peak_kind, "note": "one read + one write of every element per call"},
-            "kernels": {k: {"launches": v[0], "ms_per_step": v[1] / args.steps} for k, v in sorted(prof.items())},
-            "cpu_baseline": None, "e2e": None,
-            "gpu_launches": launches,
-            "clocks": clk,
+            "kernels": m["kernels"], "cpu_baseline": None, "e2e": None,
+            "gpu_launches": m["gpu_launches"], "clocks": clk,
         }
         print(json.dumps(line), flush=True)
     return 0
@@ -398,8 +432,9 @@ def main():
     ap.add_argument("--log2n", type=int, default=N_LOG2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="default workload: skip the batched sub-measurement")
     ap.add_argument("--cpu-sample-log2", type=int, default=26)
-    ap.add_argument("--ref-sample-log2", type=int, default=22)
+    ap.add_argument("--ref-sample-log2", type=int, default=24)
     ap.add_argument("--workload", choices=["default", "capacity-u32", "capacity-u64", "batched", "serving"],
                     default="default",
                     help="capacity-*: 2^34 elements (64 / 128 GiB) with rip_capacity_plan (k = 1024, two levels); "
@@ -572,11 +607,30 @@ def main():
         _release_host_buffers(hosts, regions)
         del hosts
 
+    # the headline's second half: one batched call over the batched workload vs one call per array
+    batched = None
+    if not args.no_batched and not capacity:
+        del x
+        torch.cuda.empty_cache()
+        batched = measure_batched(args, rip, torch, dist, ws, barrier, steps=max(args.steps, 3),
+                                  warmup=max(args.warmup, 3))
+
+    # the CPU oracle as it stands, on the host's cores: the threaded driver (root level, then the
+    # root's children concurrently) is the baseline; one thread beside it; both outputs identical
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and not capacity:
-        rate, dt, ns = cpu_oracle_sample(plan, args.cpu_sample_log2)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"2^{args.cpu_sample_log2} u64 iota with the same plan (one shuffle, {dt:.1f} s)"}
+        import numpy as np
+        pd = _plan_dict(plan)
+        cores = _host_cores()
+        rate_p, dt_p, ns, out_p = cpu_oracle_sample(pd, args.cpu_sample_log2, threads=cores)
+        rate_1, dt_1, _, out_1 = cpu_oracle_sample(pd, args.cpu_sample_log2, threads=1)
+        same = bool(np.array_equal(out_p, out_1))
+        del out_p, out_1
+        cpu = {"value": rate_p, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"2^{args.cpu_sample_log2} u64 iota with the same plan, one shuffle "
+                         f"({dt_p:.1f} s on {cores} threads: root level on one, its children on all)",
+               "single_thread": {"value": rate_1, "unit": UNIT, "cores": 1, "seconds": dt_1},
+               "outputs_identical": same}
 
     if rank == 0:
         line = {
@@ -596,6 +650,7 @@ def main():
             "whole_shuffle_roofline_frac": whole_roof_ms / ms_per_step,
             "scatter_levels": scatter_levels,
             "kernels": kernel_table,
+            "batched": batched,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": info["launches"] * args.steps,

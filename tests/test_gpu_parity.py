@@ -277,3 +277,27 @@ def test_batched_with_tuned_plans_replays_in_the_oracle():
     rip.shuffle_batched_(ts, 77, plan=plans, check=True)
     for i, (t, a, p) in enumerate(zip(ts, arrays, plans)):
         assert np.array_equal(_from_dev(t, a), oracle.shuffle(a, 77 + i, _oplan(p))), i
+
+
+@pytest.mark.parametrize("with_plans", [False, True])
+def test_batched_ex_per_array_seeds_match_the_oracle(with_plans):
+    """rip_shuffle_batched_ex (the serving loop's call): every array keeps its own 64-bit seed
+    and its default plan (or one plan per array); each equals the oracle at that seed and plan."""
+    rng = np.random.default_rng(12)
+    sizes = [0, 1, 3, 999, 4096, 9000, 33_000, 70_000, 300_001, 1 << 21]
+    seeds = [int(s) for s in rng.integers(0, 2**63, len(sizes), dtype=np.uint64)]
+    seeds[3] = 2**64 - 1  # the whole key range
+    for w in (4, 8, 16):
+        arrays = [_make(n, w) for n in sizes]
+        ts = [_to_dev(a) for a in arrays]
+        plans = None
+        if with_plans:
+            cycle = [SMEM1, INPLACE1, INPLACE2, MIXED, TINY]
+            plans = [cycle[i % len(cycle)] if sizes[i] < 400_000 else INPLACE2 for i in range(len(sizes))]
+        rip.rip_shuffle_batched_ex([t.data_ptr() for t in ts], sizes, seeds, w, plans,
+                                   stream=torch.cuda.current_stream().cuda_stream)
+        assert rip.rip_get_device_status(torch.cuda.current_stream().cuda_stream) == rip.RIP_OK
+        for i, (t, a) in enumerate(zip(ts, arrays)):
+            p = _oplan(plans[i]) if plans else _default_oplan(sizes[i], w)
+            want = oracle.shuffle(a, seeds[i], p)
+            assert np.array_equal(_from_dev(t, a), want), (w, i, sizes[i])

@@ -56,3 +56,35 @@ def test_noalloc_rejects_inputs_beyond_its_workspace():
     assert "too large" in rip.rip_strerror(rc)
     torch.cuda.synchronize()
     assert torch.equal(x, torch.arange(n * w // 8, dtype=torch.int64, device="cuda"))  # untouched
+
+
+def test_noalloc_takes_no_device_memory():
+    """After the library's managed workspace is released, two rip_shuffle_noalloc calls leave the
+    device's free memory where it was (the kernels are loaded by a first call beforehand)."""
+    lib = rip._load()
+    stream = torch.cuda.current_stream().cuda_stream
+    n, w = 1 << 20, 4
+    x = _tensor(n, w)
+    assert lib.rip_shuffle_noalloc(ctypes.c_void_p(x.data_ptr()), n, w, 1, None, ctypes.c_void_p(stream)) == 0
+    torch.cuda.synchronize()
+    rip.rip_release_workspace()
+    free0, _ = torch.cuda.mem_get_info()
+    for seed in (2, 3):
+        rc = lib.rip_shuffle_noalloc(ctypes.c_void_p(x.data_ptr()), n, w, seed, None, ctypes.c_void_p(stream))
+        assert rc == rip.RIP_OK
+    assert lib.rip_get_device_status(ctypes.c_void_p(stream)) == rip.RIP_OK
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0, (free0, free1)
+
+
+def test_documented_sizes_fit_the_fixed_workspace():
+    """The header's promise: with the default plans, every power-of-two size up to 2^27 4-byte,
+    2^26 8-byte and 2^20 16-byte elements fits the fixed array (the plans do not depend on the
+    device, so neither does this)."""
+    for w, top in ((4, 27), (8, 26), (16, 20)):
+        for e in range(1, top + 1):
+            assert 0 < rip.rip_shuffle_workspace_size(1 << e, w) <= rip_noalloc_ws_bytes(), (w, e)
+
+
+def rip_noalloc_ws_bytes():
+    return 32 << 20  # RIP_NOALLOC_WS_BYTES in include/rip_shuffle.h
