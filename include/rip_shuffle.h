@@ -186,8 +186,8 @@ int rip_debug_fail_allocations(uint32_t count);
 /* Testing hook for the bounded device-side waits: later calls give every
  * hand-off wait of the classify step (input arrived, chunks read out, round
  * placed) and every chain wait of the block permutation at most `polls`
- * polls (the first one non-blocking) instead of the built-in limits (2^26
- * mbarrier polls, 2^24 spins).  A wait that runs out records RIP_ETIMEOUT;
+ * polls (the first one non-blocking) instead of the built-in limits (2^20
+ * mbarrier polls of up to 4 us each, 2^24 spins).  A wait that runs out records RIP_ETIMEOUT;
  * the kernel finishes its own copies in flight and returns, the call's later
  * kernels skip their work, and rip_get_device_status reports RIP_ETIMEOUT.
  * The data of that call are then not a valid shuffle.  polls 0 restores the

@@ -71,6 +71,8 @@ def _load():
         lib.oracle_shuffle_batched.restype = i32
         lib.oracle_shuffle_many.argtypes = [vp, u64, u32, u64, u64, u32, vp, vp, vp, u64, u32, vp]
         lib.oracle_shuffle_many.restype = i32
+        lib.oracle_splitmix64.argtypes = [u64]
+        lib.oracle_splitmix64.restype = u64
         lib.oracle_hash.argtypes = [vp, u64, u32]
         lib.oracle_hash.restype = u64
         lib.oracle_hash_at.argtypes = [vp, u64, u32, u64]
@@ -237,6 +239,11 @@ def shuffle_many(template: np.ndarray, seed0: int, count: int, plan: Plan) -> np
     if rc:
         raise RuntimeError("oracle_shuffle_many failed")
     return out
+
+
+def splitmix64(x: int) -> int:
+    """The splitmix64 finaliser of the digest (Steele, Lea, Flood 2014): f(x + 0x9E3779B97F4A7C15)."""
+    return int(_load().oracle_splitmix64(int(x) & 0xFFFFFFFFFFFFFFFF))
 
 
 def digest(a: np.ndarray) -> int:

@@ -354,6 +354,9 @@ static uint64_t splitmix64(uint64_t x)
     return z ^ (z >> 31);
 }
 
+/* The finaliser above, exported so tests can pin it to published outputs. */
+uint64_t oracle_splitmix64(uint64_t x) { return splitmix64(x); }
+
 /* Position-dependent 64-bit digest of an array:
  *   H = sum_p splitmix64(p * 0x9E3779B97F4A7C15 ^ v(p))  (mod 2^64),
  *   v = chain of splitmix64 over the element's 8-byte little-endian words

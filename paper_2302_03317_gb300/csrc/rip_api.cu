@@ -215,6 +215,12 @@ Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& 
         const double d = t - mu;
         return std::exp(-d * d / (2.0 * (mu + d / 3.0)));
     };
+    // lower tail: P(size <= t) for t below the mean mu is at most exp(-(mu - t)^2 / (2 mu)) (Chernoff)
+    auto lower = [](double mu, double t) {
+        if (t >= mu) return 1.0;
+        const double d = mu - t;
+        return std::exp(-d * d / (2.0 * mu));
+    };
     double e_med = 0, e_big = 0;
     for (uint64_t n : ns) {
         if (n > L.small_max_m && n <= kMediumMaxM) e_med += 1;
@@ -288,7 +294,8 @@ Layout make_layout(const std::vector<uint64_t>& ns, uint32_t w, const rip_plan& 
         }
         max_children = std::max<uint64_t>(max_children, (uint64_t)c.big * k);
         const double mu_child = (double)nmax / ((double)prodk * k);
-        e_med += (double)c.big * k * tail(mu_child, (double)L.small_max_m);
+        // medium children: above the on-SM limit and at most kMediumMaxM (larger ones run in place)
+        e_med += (double)c.big * k * std::min(tail(mu_child, (double)L.small_max_m), lower(mu_child, (double)kMediumMaxM));
         e_big += (double)c.big * k * tail(mu_child, (double)kMediumMaxM);
         caps.push_back(c);
         small_children += (uint64_t)c.big * k;

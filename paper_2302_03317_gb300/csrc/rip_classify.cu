@@ -284,12 +284,11 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                     }
                     if (issued) {
                         bulk_commit();
-                        if (rr + 1 == nrounds) {
-                            bulk_wait_all();  // the tails read open blocks back
-                            fence_proxy_async_global();
-                        } else {
-                            bulk_wait_read();
-                        }
+                        bulk_wait_read();
+                    }
+                    if (rr + 1 == nrounds) {  // the tails read open blocks back: every store is complete
+                        bulk_wait_all();
+                        fence_proxy_async_global();
                     }
                 } else {
                     for (uint32_t f = 0; f < nf; ++f) {
@@ -371,11 +370,21 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                         if (mine) {
                             uint16_t* col = tbl + b * S;
                             if constexpr (KB > 0) {
+                                // loads first, in batches of eight: the stores cannot alias them,
+                                // but the compiler cannot tell, and would wait for each load in turn
+                                constexpr uint32_t NW = cls_nwr(KC, W);
 #pragma unroll
-                                for (uint32_t j = 0; j < cls_nwr(KC, W); ++j) {
-                                    const uint32_t c = col[j];
-                                    col[j] = (uint16_t)acc;
-                                    acc += c;
+                                for (uint32_t j0 = 0; j0 < NW; j0 += 8) {
+                                    uint32_t cv[8];
+#pragma unroll
+                                    for (uint32_t j = 0; j < 8; ++j)
+                                        if (j0 + j < NW) cv[j] = col[j0 + j];
+#pragma unroll
+                                    for (uint32_t j = 0; j < 8; ++j)
+                                        if (j0 + j < NW) {
+                                            col[j0 + j] = (uint16_t)acc;
+                                            acc += cv[j];
+                                        }
                                 }
                             } else {
                                 for (uint32_t j = 0; j < nwr; ++j) {

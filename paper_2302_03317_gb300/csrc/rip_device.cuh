@@ -314,7 +314,8 @@ __device__ __forceinline__ uint64_t phys_index(const Sub& s, uint64_t i) {
 
 // ----------------------------------------------------------------- mbarriers and bulk copies
 
-constexpr uint32_t kMbarPolls = 1u << 26;  // mbarrier polls before a wait gives up
+constexpr uint32_t kMbarPolls = 1u << 20;     // mbarrier polls before a wait gives up
+constexpr uint32_t kMbarSuspendNs = 4000;     // each poll sleeps up to this long (about 4 s in all)
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -334,7 +335,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 // Bounded wait for the phase with the given parity: one non-blocking test, then up to
-// polls - 1 potentially blocking tries; false when the phase has not completed by then.
+// polls - 1 tries, each of which suspends the thread until the phase completes or
+// kMbarSuspendNs pass (a waiting warp then issues nothing, instead of spinning on issue slots
+// the working warps need); false when the phase has not completed by then.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t polls = kMbarPolls) {
     const uint32_t a = smem_addr(bar);
     uint32_t done;
@@ -346,9 +349,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
     if (done) return true;
     for (uint32_t i = 1; i < polls; ++i) {
         asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
-            : "r"(a), "r"(parity)
+            : "r"(a), "r"(parity), "r"(kMbarSuspendNs)
             : "memory");
         if (done) return true;
     }

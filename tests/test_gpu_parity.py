@@ -301,3 +301,4 @@ def test_batched_ex_per_array_seeds_match_the_oracle(with_plans):
             p = _oplan(plans[i]) if plans else _default_oplan(sizes[i], w)
             want = oracle.shuffle(a, seeds[i], p)
             assert np.array_equal(_from_dev(t, a), want), (w, i, sizes[i])
+

@@ -418,3 +418,17 @@ def test_digest_is_a_sum_over_pieces():
     parts = [(0, 1), (1, 4000), (4000, 10_000)]
     h = sum(int(lib.oracle_hash_at(a[x:y].ctypes.data, y - x, 8, x)) for x, y in parts) & (2**64 - 1)
     assert h == oracle.digest(a)
+
+
+def test_splitmix64_matches_the_published_generator():
+    """splitmix64 as published (Steele, Lea and Flood, OOPSLA 2014; Vigna's reference C code):
+    the generator started from state 0 adds 0x9E3779B97F4A7C15 and applies the finaliser, so its
+    first three outputs are the finaliser of phi, 2 phi, 3 phi -- i.e. splitmix64(0), (phi),
+    (2 phi) in this code's convention.  Pins the digest's mixer (oracle) and the record
+    payloads (input generator) alike."""
+    from paper_2302_03317_gb300.inputs import splitmix64_np
+    phi = 0x9E3779B97F4A7C15
+    published = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    xs = [0, phi, (2 * phi) % 2**64]
+    assert [oracle.splitmix64(x) for x in xs] == published
+    assert [int(v) for v in splitmix64_np(np.array(xs, dtype=np.uint64))] == published
