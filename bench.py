@@ -321,7 +321,43 @@ def measure_batched(args, rip, torch, dist, ws, barrier, steps, warmup):
     rc = rip.rip_get_device_status(stream.cuda_stream)
     if rc != 0:
         raise SystemExit(f"device status after batched steps: {rip.rip_strerror(rc)}")
-    del buf, views
+
+    # the same batched call captured once in a CUDA graph (caller workspace, no host copies) and
+    # replayed: no per-call host work and no launch gaps between the ~340 kernels
+    ns = [int(v.shape[0]) for v in views]
+    ptrs = [v.data_ptr() for v in views]
+    gplans = plans if plans else [rip.rip_default_plan(n, 4) for n in ns]
+    gneed = rip.rip_shuffle_batched_plans_workspace_size(ns, 4, gplans)
+    gws = torch.empty(max(gneed, 256), dtype=torch.uint8, device="cuda")
+    gs = torch.cuda.Stream()
+
+    def gcall(seed):
+        rip.rip_shuffle_batched_plans(ptrs, ns, 4, seed, gplans, gws.data_ptr(), gneed, gs.cuda_stream)
+
+    gs.wait_stream(stream)
+    with torch.cuda.stream(gs):
+        gcall(SEED + 3)  # on the capturing stream first: its auxiliary streams, kernel attributes
+    gs.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=gs):
+        gcall(SEED + 5)
+    for _ in range(warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    barrier()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(gs)
+    with torch.cuda.stream(gs):
+        for _ in range(steps):
+            graph.replay()
+    g1.record(gs)
+    torch.cuda.synchronize()
+    barrier()
+    ms_g = max_over_ranks(g0.elapsed_time(g1), dist, "cuda") / steps
+    rc = rip.rip_get_device_status(gs.cuda_stream)
+    if rc != 0:
+        raise SystemExit(f"device status after graph replays: {rip.rip_strerror(rc)}")
+    del graph, gws, buf, views
     value = job_rate(ws, total, ms_b)
     plain_rate = job_rate(ws, total, ms_p)
     return {"value": value, "unit": UNIT, "ms_per_step": ms_b, "steps": steps, "arrays": args.arrays,
@@ -332,6 +368,8 @@ def measure_batched(args, rip, torch, dist, ws, barrier, steps, warmup):
             "plain": {"value": plain_rate, "unit": UNIT, "ms_per_step": ms_p,
                       "how": "one rip_shuffle call per array, same plans, seeds and results"},
             "vs_plain": value / plain_rate,
+            "graph": {"value": job_rate(ws, total, ms_g), "unit": UNIT, "ms_per_step": ms_g,
+                      "how": "the batched call captured once in a CUDA graph (caller workspace) and replayed"},
             "kernels": {k: {"launches": v[0], "ms_per_step": v[1] / steps} for k, v in sorted(prof.items())},
             "gpu_launches": launches}
 
@@ -352,7 +390,7 @@ def run_batched(args, rip, torch, dist, ws, rank, local, barrier):
             "config": {"workload": "batched: " + m["workload"], "arrays": args.arrays, "elements": total,
                        "elem_bytes": 4, "l2": f"{total * 4 / 2**30:.1f} GiB of arrays vs 129 MB L2",
                        "parallelism": f"replicas{ws}" if ws > 1 else "single"},
-            "plain": m["plain"], "vs_plain": m["vs_plain"],
+            "plain": m["plain"], "vs_plain": m["vs_plain"], "graph": m["graph"],
             "roofline": {"bound": "hbm", "kernel": "whole batched call", "achieved": 2 * 4 * total / (ms_b / 1e3) / 1e9,
                          "peak": hbm_gbs, "unit": "GB/s",
                          "frac": 2 * 4 * total / (ms_b / 1e3) / 1e9 / hbm_gbs, "traffic": None,

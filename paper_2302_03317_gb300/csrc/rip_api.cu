@@ -66,6 +66,25 @@ struct Profiler {
 Profiler g_prof;
 }  // namespace
 
+cudaError_t ensure_dyn_smem(const void* func, int bytes) {
+    static std::mutex m;
+    static std::vector<std::pair<std::pair<int, const void*>, int>> set;  // (device, kernel) -> bytes
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    std::lock_guard<std::mutex> lock(m);
+    for (auto& e : set)
+        if (e.first.first == dev && e.first.second == func) {
+            if (e.second >= bytes) return cudaSuccess;
+            err = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            if (err == cudaSuccess) e.second = bytes;
+            return err;
+        }
+    err = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (err == cudaSuccess) set.push_back({{dev, func}, bytes});
+    return err;
+}
+
 void prof_begin(const char* name, cudaStream_t s) {
     if (!g_prof.on) return;
     cudaEvent_t e = g_prof.get();
@@ -539,13 +558,22 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
         aligned16 &= (reinterpret_cast<uintptr_t>(ptrs[i]) % 16) == 0;
     }
     ArrayDesc* d_arr = reinterpret_cast<ArrayDesc*>(wsp + lay.arrays);
+    uint32_t launches = 0;
     InitArgs ia{};
-    if (arr.size() <= kInlineArrays) {  // written by the init kernel: no host copy, no stream sync
+    // the table reaches the device in kernel parameters, never by a copy from host memory: no
+    // stream sync, and a captured CUDA graph holds the table itself
+    if (arr.size() <= kInlineArrays) {  // written by the init kernel
         ia.inline_count = (uint32_t)arr.size();
         for (size_t i = 0; i < arr.size(); ++i) ia.inline_arrays[i] = arr[i];
-    } else if (cudaMemcpyAsync(d_arr, arr.data(), sizeof(ArrayDesc) * arr.size(), cudaMemcpyHostToDevice,
-                               stream) != cudaSuccess) {
-        return RIP_ECUDA;
+    } else {
+        for (size_t i0 = 0; i0 < arr.size(); i0 += kDescsPerLaunch) {
+            DescChunk c{};
+            c.dst = d_arr + i0;
+            c.n = (uint32_t)std::min<size_t>(kDescsPerLaunch, arr.size() - i0);
+            for (uint32_t j = 0; j < c.n; ++j) c.a[j] = arr[i0 + j];
+            if (launch_descs(c, stream) != cudaSuccess) return RIP_ECUDA;
+            ++launches;
+        }
     }
 
     uint32_t* counts = reinterpret_cast<uint32_t*>(wsp + lay.counts);
@@ -568,7 +596,6 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
     uint32_t* counters = reinterpret_cast<uint32_t*>(wsp + lay.counters);
     uint64_t* pool_used = reinterpret_cast<uint64_t*>(wsp + lay.pool_used);
     Status* cst = reinterpret_cast<Status*>(wsp + lay.cstatus);  // this call's status word
-    uint32_t launches = 0;
 
     ia.arrays = d_arr;
     ia.narrays = (uint32_t)arr.size();

@@ -694,7 +694,7 @@ bool classify_config(uint32_t k, uint32_t B, uint32_t w, ClsCfg* out) {
 template <int W, int KB>
 static cudaError_t launch_cls(const LevelArgs& a, uint32_t num_sms, cudaStream_t s) {
     const int smem = (int)a.cls.bytes;
-    cudaError_t err = cudaFuncSetAttribute(classify_kernel<W, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t err = ensure_dyn_smem(reinterpret_cast<const void*>(classify_kernel<W, KB>), smem);
     if (err != cudaSuccess) return err;
     classify_kernel<W, KB><<<num_sms, kClassifyThreads, smem, s>>>(a);
     return cudaGetLastError();

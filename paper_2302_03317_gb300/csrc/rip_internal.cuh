@@ -163,6 +163,22 @@ struct SmallArgs {
 };
 
 constexpr uint32_t kInlineArrays = 4;
+constexpr uint32_t kDescsPerLaunch = 160;  // array descriptors carried by one descs_kernel's parameters
+
+// A piece of a call's array table, written to the workspace by a kernel that carries it in its
+// parameters (no host copy: the call can be captured in a CUDA graph).
+struct DescChunk {
+    ArrayDesc* dst;
+    uint32_t n;
+    uint32_t pad;
+    ArrayDesc a[kDescsPerLaunch];
+};
+static_assert(sizeof(DescChunk) <= 4096, "kernel parameters stay within the classic 4 KB limit");
+
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) only when the kernel's setting on the current
+// device is below `bytes` (rip_api.cu): calls made while a stream is being captured into a CUDA
+// graph then issue no attribute calls once the same shapes ran before.
+cudaError_t ensure_dyn_smem(const void* func, int bytes);
 
 struct InitArgs {
     ArrayDesc* arrays;
@@ -199,6 +215,7 @@ cudaError_t launch_classify(const LevelArgs& a, uint32_t w, uint32_t num_sms, cu
 size_t permute_smem_bytes(uint32_t B, uint32_t w);
 uint32_t permute_threads(uint32_t B, uint32_t w);
 cudaError_t launch_init(const InitArgs& a, cudaStream_t s);
+cudaError_t launch_descs(const DescChunk& c, cudaStream_t s);
 cudaError_t launch_level(const LevelArgs& a, uint32_t w, uint32_t num_sms, cudaStream_t s, uint32_t* launches);
 // The call's last kernel: copies the call's status word into the device's (global) one, then
 // finishes leaves too large for one SM.

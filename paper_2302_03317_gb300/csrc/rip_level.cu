@@ -110,6 +110,10 @@ __global__ void init_kernel(InitArgs a) {
     }
 }
 
+__global__ void descs_kernel(DescChunk c) {
+    for (uint32_t i = threadIdx.x; i < c.n; i += blockDim.x) c.dst[i] = c.a[i];
+}
+
 // ------------------------------------------------------------------ tiles
 
 __global__ void tiles_kernel(LevelArgs a) {
@@ -644,6 +648,12 @@ size_t permute_smem_bytes(uint32_t B, uint32_t w) {
     return (size_t)(permute_threads(B, w) / kGroup) * 2u * B * w;
 }
 
+cudaError_t launch_descs(const DescChunk& c, cudaStream_t s) {
+    ProfScope p("descs", s);
+    descs_kernel<<<1, 160, 0, s>>>(c);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init(const InitArgs& a, cudaStream_t s) {
     ProfScope p("init", s);
     init_kernel<<<1, 256, 0, s>>>(a);
@@ -672,13 +682,13 @@ static cudaError_t launch_level_w(const LevelArgs& a, uint32_t num_sms, cudaStre
     const size_t psm = permute_smem_bytes(a.B, W);
     const uint32_t pgrid = num_sms * 8u * (kPermuteThreads / pthreads);
     if (a.vec16) {
-        err = cudaFuncSetAttribute(permute_kernel<uint4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
+        err = ensure_dyn_smem(reinterpret_cast<const void*>(permute_kernel<uint4>), (int)psm);
         if (err != cudaSuccess) return err;
         ProfScope p("permute", s);
         permute_kernel<uint4><<<pgrid, pthreads, psm, s>>>(a, W);
     } else {
         using T = typename Elem<W>::T;
-        err = cudaFuncSetAttribute(permute_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
+        err = ensure_dyn_smem(reinterpret_cast<const void*>(permute_kernel<T>), (int)psm);
         if (err != cudaSuccess) return err;
         ProfScope p("permute", s);
         permute_kernel<T><<<pgrid, pthreads, psm, s>>>(a, W);

@@ -778,17 +778,17 @@ cudaError_t launch_small(const SmallArgs& args_in, uint32_t w, size_t smem, uint
     ProfScope p(args.medium ? "solve_medium" : "solve_small", stream);
     switch (w) {
         case 4:
-            err = cudaFuncSetAttribute(small_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            err = ensure_dyn_smem(reinterpret_cast<const void*>(small_kernel<4>), (int)smem);
             if (err != cudaSuccess) return err;
             small_kernel<4><<<grid, kThreads, smem, stream>>>(args);
             break;
         case 8:
-            err = cudaFuncSetAttribute(small_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            err = ensure_dyn_smem(reinterpret_cast<const void*>(small_kernel<8>), (int)smem);
             if (err != cudaSuccess) return err;
             small_kernel<8><<<grid, kThreads, smem, stream>>>(args);
             break;
         default:
-            err = cudaFuncSetAttribute(small_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            err = ensure_dyn_smem(reinterpret_cast<const void*>(small_kernel<16>), (int)smem);
             if (err != cudaSuccess) return err;
             small_kernel<16><<<grid, kThreads, smem, stream>>>(args);
             break;
