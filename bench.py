@@ -407,53 +407,64 @@ def run_serving(args, rip, torch, dist, ws, rank, local, barrier):
     log-uniform in [2^10, 2^26], element width uniform over 4, 8 and 16 bytes, admitted under a
     64 GiB device-memory budget and batched as they arrive (serve.py).  Latency = completion
     seen by the server minus arrival; throughput = elements of all requests over the span from
-    the first arrival to the last completion."""
+    the first arrival to the last completion.  The same stream thinned to `--light-rate`
+    requests/s (below saturation) is measured as well, so the latency figures separate queueing
+    under overload from service time."""
     import numpy as np
     from paper_2302_03317_gb300.serve import Request, run_session
 
-    def requests(count, seed):
+    def requests(count, seed, rate):
         rng = np.random.default_rng(seed)
-        t = np.cumsum(rng.exponential(1.0 / 2000.0, count))
+        t = np.cumsum(rng.exponential(1.0 / rate, count))
         sizes = np.floor(2.0 ** (10 + 16 * rng.random(count))).astype(np.int64)
         widths = rng.choice([4, 8, 16], count)
         return [Request(i, int(n), int(w), seed=SEED + i, arrive=float(a))
                 for i, (a, n, w) in enumerate(zip(t, sizes, widths))]
 
     budget = 64 << 30
+
+    def session(rate, count):
+        reqs = requests(count, SEED, rate)
+        barrier()
+        srv = run_session(reqs, budget)
+        torch.cuda.synchronize()
+        barrier()
+        rc = rip.rip_get_device_status(torch.cuda.current_stream().cuda_stream)
+        if rc != 0:
+            raise SystemExit(f"device status after the session: {rip.rip_strerror(rc)}")
+        fin = srv.finished
+        lat = np.array(sorted(r.done - r.arrive for r in fin)) * 1e3
+        span = max(r.done for r in fin) - min(r.arrive for r in fin)
+        elems = sum(r.n for r in fin)
+        arrive_span = max(r.arrive for r in reqs) - min(r.arrive for r in reqs)
+        return {"rate_req_per_s": rate, "requests": len(fin), "elements": elems, "bytes": sum(r.nbytes for r in fin),
+                "value": job_rate(ws, elems, span * 1e3), "unit": UNIT, "span_ms": span * 1e3,
+                "offered_rate_elems_per_s": elems / arrive_span if arrive_span > 0 else None,
+                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
+                               "p99": float(np.percentile(lat, 99)), "max": float(lat[-1])},
+                "batches": srv.batches, "mean_batch": len(fin) / max(srv.batches, 1)}
+
     for i in range(args.warmup):  # warm-up sessions (allocator, library workspace, streams)
-        run_session(requests(64, SEED + 100 + i), budget)
+        run_session(requests(64, SEED + 100 + i, 2000.0), budget)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    reqs = requests(args.requests, SEED)
-    barrier()
-    srv = run_session(reqs, budget)
-    torch.cuda.synchronize()
-    barrier()
+    main = session(2000.0, args.requests)
+    light = session(args.light_rate, max(50, args.requests // 4))
     clk = clocks.stop()
-    rc = rip.rip_get_device_status(torch.cuda.current_stream().cuda_stream)
-    if rc != 0:
-        raise SystemExit(f"device status after the session: {rip.rip_strerror(rc)}")
-    fin = srv.finished
-    lat = np.array(sorted(r.done - r.arrive for r in fin)) * 1e3
-    span = max(r.done for r in fin) - min(r.arrive for r in fin)
-    elems = sum(r.n for r in fin)
-    nbytes = sum(r.nbytes for r in fin)
-    value = job_rate(ws, elems, span * 1e3)
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": 1,
-            "warmup": args.warmup, "ms_per_step": span * 1e3, "higher_is_better": True, "scaling": "weak",
+            "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": ws, "steps": 1,
+            "warmup": args.warmup, "ms_per_step": main["span_ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32/u64/16-byte records", "data": "synthetic",
             "config": {"workload": f"serving: {args.requests} requests, Poisson arrivals at 2000/s, sizes "
                                    "log-uniform in [2^10, 2^26], widths uniform over 4/8/16 bytes, 64 GiB budget",
-                       "requests": len(fin), "elements": elems, "bytes": nbytes,
-                       "offered_rate_elems_per_s": elems / (max(r.arrive for r in reqs) - min(r.arrive for r in reqs)),
+                       "requests": main["requests"], "elements": main["elements"], "bytes": main["bytes"],
+                       "offered_rate_elems_per_s": main["offered_rate_elems_per_s"],
                        "parallelism": f"replicas{ws}" if ws > 1 else "single"},
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
-                           "p99": float(np.percentile(lat, 99)), "max": float(lat[-1])},
-            "batches": srv.batches, "mean_batch": len(fin) / max(srv.batches, 1),
+            "latency_ms": main["latency_ms"], "batches": main["batches"], "mean_batch": main["mean_batch"],
+            "below_saturation": light,
             "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None,
             "clocks": clk,
         }
@@ -479,6 +490,8 @@ def main():
                          "batched: 4096 u32 arrays, sizes log-uniform in [2^8, 2^20], one batched call vs one call per array")
     ap.add_argument("--arrays", type=int, default=4096)
     ap.add_argument("--requests", type=int, default=800, help="serving: requests of the arrival stream")
+    ap.add_argument("--light-rate", type=float, default=500.0,
+                    help="serving: arrival rate (requests/s) of the second, lighter stream")
     ap.add_argument("--plans", choices=["tuned", "default"], default="tuned",
                     help="batched: per-size-class plans from the tuner's table (if present) or default plans")
     ap.add_argument("--ks", type=str, default="", help="profiling: comma list of k per level (overrides the default plan)")
