@@ -619,7 +619,7 @@ int run_shuffle(const std::vector<char*>& ptrs, const std::vector<uint64_t>& ns,
                      wsp + lay.mscratch, (uint64_t)kMediumMaxM * w, 1};
         const size_t msmem = small_smem_bytes(kMediumMaxM, w, true);
         if (launch_small(ma, w, msmem, lay.medium_grid, stream) != cudaSuccess) return RIP_ECUDA;
-        launches += 2;
+        launches += 3;  // the on-SM solver, its index-path leaves, the medium solver
         return RIP_OK;
     };
     int rc = run_small();

@@ -205,6 +205,7 @@ struct ProfScope {
 // rip_small.cu
 size_t small_fixed_smem();
 size_t small_smem_bytes(uint64_t m, uint32_t w, bool medium);
+// the on-SM solver (small_kernel) and, unless medium, the leaves it leaves to leaf_kernel
 cudaError_t launch_small(const SmallArgs& args, uint32_t w, size_t smem, uint32_t grid, cudaStream_t stream);
 
 // rip_classify.cu

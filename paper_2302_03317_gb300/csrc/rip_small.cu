@@ -148,6 +148,54 @@ __device__ void fy_parallel_data(T* D, const uint16_t* H, RT* R, uint32_t len, S
     __syncthreads();
 }
 
+// The same rounds with 32-bit reservations stamped by the round (round << 16 | step): an entry of
+// an earlier round loses every comparison, so nothing is cleared between rounds.  Z is the data
+// itself, or 16-bit indices whose final order a gather applies to the data afterwards.
+template <typename T>
+__device__ void fy_parallel_stamped(T* Z, const uint16_t* H, uint32_t* R, uint32_t len, Status* status) {
+    __shared__ uint32_t remaining;
+    const uint32_t nb = blockDim.x, tid = threadIdx.x;
+    uint64_t mine = 0;
+    for (uint32_t j = 0; j < 64u && tid + j * nb < len; ++j)
+        if (tid + j * nb >= 1u) mine |= 1ull << j;  // step 0 does nothing
+    for (uint32_t i = tid; i < len; i += nb) R[i] = 0;
+    for (uint32_t round = 1;; ++round) {
+        __syncthreads();
+        if (tid == 0) remaining = 0;
+        for (uint64_t mk = mine; mk; mk &= mk - 1) {
+            const uint32_t i = tid + (uint32_t)(__ffsll((long long)mk) - 1) * nb;
+            const uint32_t tag = (round << 16) | i;
+            atomicMax(&R[i], tag);
+            atomicMax(&R[H[i]], tag);
+        }
+        __syncthreads();
+        uint64_t left = 0;
+        for (uint64_t mk = mine; mk; mk &= mk - 1) {
+            const uint32_t j = (uint32_t)(__ffsll((long long)mk) - 1);
+            const uint32_t i = tid + j * nb;
+            const uint32_t h = H[i];
+            const uint32_t tag = (round << 16) | i;
+            if (R[i] == tag && R[h] == tag) {
+                const T zi = Z[i];
+                Z[i] = Z[h];
+                Z[h] = zi;
+            } else {
+                left |= 1ull << j;
+            }
+        }
+        if (left) remaining = 1;
+        __syncthreads();
+        const bool again = remaining != 0;
+        mine = left;
+        if (!again) break;
+        if (round >= 0xFFFFu) {  // cannot happen: the latest unfinished step always commits
+            if (tid == 0) report(status, RIP_EINTERNAL, 0x510A, len);
+            break;
+        }
+    }
+    __syncthreads();
+}
+
 __device__ void fy_block(uint16_t* Z, uint16_t* draws, uint32_t len, PhiloxKey key, uint32_t L,
                          uint64_t leaf_o) {
     for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
@@ -579,6 +627,119 @@ __device__ void scatter_range(SmallShared& sh, uint16_t* P0, uint16_t* P1, uint3
                     [&](uint32_t b) { return sh.g.fb[b]; });
 }
 
+// Starts the bulk (TMA) loads of a subproblem's data into shared memory after P1, through its
+// rotation, completing on load_bar; the threads copy the ragged rest.  Returns where the data go.
+template <int W>
+__device__ __forceinline__ typename Elem<W>::T* load_smem(const Sub& s, typename Elem<W>::T* base, uint32_t m,
+                                                         uint16_t* P1, uint64_t* load_bar) {
+    using T = typename Elem<W>::T;
+    const uint32_t tid = threadIdx.x;
+    T* D;
+    // the rotation's pieces: logical [0, nA) from physical o+eps.., [nA, m) from o..; each
+    // piece's 16-byte-aligned middle goes by bulk copy when its shared-memory start is
+    // aligned too (the larger piece fixes D's shift), the rest by the threads
+    const uint32_t q = W >= 16 ? 1u : 16u / W;  // elements per 16 bytes
+    const uint32_t nA = m - s.eps;
+    const uintptr_t gA = reinterpret_cast<uintptr_t>(base + s.o + s.eps);
+    const uintptr_t gB = reinterpret_cast<uintptr_t>(base + s.o);
+    auto first_aligned = [&](uint32_t L0, uint32_t L1, uintptr_t g) -> uint32_t {
+        return min(L1, L0 + (uint32_t)(((16u - (g & 15u)) & 15u) / W));
+    };
+    const uint32_t fa = first_aligned(0u, nA, gA), fb = first_aligned(nA, m, gB);
+    const uint32_t dshift = nA >= s.eps ? (q - fa % q) % q : (q - fb % q) % q;
+    D = reinterpret_cast<T*>(P1 + ((m + 7u) & ~7u)) + dshift;
+    auto bulk_range = [&](uint32_t L0, uint32_t L1, uintptr_t g, uint32_t f, uint32_t& lo, uint32_t& hi) {
+        lo = hi = L0;
+        const uint32_t e = f + (L1 - f) / q * q;
+        if (e > f && ((g + (uintptr_t)(f - L0) * W) & 15u) == 0 && (dshift + f) % q == 0) {
+            lo = f;
+            hi = e;
+        }
+    };
+    uint32_t aLo, aHi, bLo, bHi;
+    bulk_range(0u, nA, gA, fa, aLo, aHi);
+    bulk_range(nA, m, gB, fb, bLo, bHi);
+    if (bLo == bHi) bLo = bHi = m;
+    if (tid == 0) {
+        const uint32_t bytes = (aHi - aLo + bHi - bLo) * (uint32_t)W;
+        if (bytes) {
+            mbar_arrive_expect_tx(load_bar, bytes);
+            auto issue = [&](uint32_t lo, uint32_t hi, uintptr_t g, uint32_t L0) {
+                const char* src = reinterpret_cast<const char*>(g + (uintptr_t)(lo - L0) * W);
+                char* dst = reinterpret_cast<char*>(D + lo);
+                const uint32_t nbytes = (hi - lo) * (uint32_t)W;
+                for (uint32_t off = 0; off < nbytes; off += 32768u)
+                    bulk_g2s(dst + off, src + off, min(32768u, nbytes - off), load_bar);
+            };
+            if (aHi > aLo) issue(aLo, aHi, gA, 0u);
+            if (bHi > bLo) issue(bLo, bHi, gB, nA);
+        } else {
+            mbar_arrive(load_bar);
+        }
+    }
+    for (uint32_t i = tid; i < aLo; i += blockDim.x) D[i] = base[phys_index(s, i)];
+    for (uint32_t i = aHi + tid; i < bLo; i += blockDim.x) D[i] = base[phys_index(s, i)];
+    for (uint32_t i = bHi + tid; i < m; i += blockDim.x) D[i] = base[phys_index(s, i)];
+    return D;
+}
+
+// Leaves handled by leaf_kernel: Fisher-Yates leaves in shared memory whose 32-bit reservations do
+// not fit after the data but 8 bytes per element of indices, draws and reservations do.
+__device__ __forceinline__ bool leaf_by_index(const SmallArgs& args, const Sub& s, uint32_t w) {
+    const uint64_t m = s.m, mr = (m + 7u) & ~7ull;
+    return !args.medium && m > 1 && m <= 64u * kThreads && args.plan.is_leaf(m, s.level) &&
+           8 * mr + w * mr + 16 > args.dyn_bytes && 8 * mr <= args.dyn_bytes;
+}
+
+// A Fisher-Yates leaf whose 32-bit reservations do not fit beside its data (8- and 16-byte
+// elements near the on-SM limit): the steps run on 16-bit indices (indices, draws and stamped
+// reservations take 8 bytes per element), then the data are loaded into the space the draws and
+// reservations held and written back gathered through the indices.  Run by leaf_kernel, not by
+// small_kernel, whose register allocation any added path perturbs.  False when the load's wait
+// expired (reported).
+template <int W>
+__device__ __forceinline__ bool fy_leaf_by_index(const SmallArgs& args, const Sub& s, typename Elem<W>::T* base,
+                                              uint32_t m, PhiloxKey key, unsigned char* dyn, uint64_t* load_bar,
+                                              uint32_t parity, uint32_t item) {
+    using T = typename Elem<W>::T;
+    const uint32_t tid = threadIdx.x;
+    const uint64_t mr = (m + 7u) & ~7u;
+    uint16_t* Z = reinterpret_cast<uint16_t*>(dyn);
+    uint16_t* H = Z + mr;
+    for (uint32_t i = tid; i < m; i += blockDim.x) Z[i] = (uint16_t)i;
+    fy_draws(H, m, key, s.level, s.o);  // ends with a barrier
+    fy_parallel_stamped(Z, H, reinterpret_cast<uint32_t*>(dyn + 4 * mr), m, args.status);
+    fence_proxy_async_smem();  // the reservations' bytes become the bulk copy's destination
+    __syncthreads();
+    const T* D = load_smem<W>(s, base, m, H, load_bar);
+    const bool ok = __syncthreads_and(mbar_wait(load_bar, parity)) != 0;
+    if (!ok) {
+        if (tid == 0) report(args.status, RIP_ETIMEOUT, 0x510B, item);
+        return false;
+    }
+    for (uint32_t i0 = tid; i0 < m; i0 += 4u * blockDim.x) {  // four gathers in flight per thread
+        uint32_t j[4];
+        T v[4];
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u) {
+            const uint32_t i = i0 + u * blockDim.x;
+            j[u] = i < m ? (uint32_t)Z[i] : 0u;
+        }
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u)
+            if (j[u] < m) v[u] = D[j[u]];
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u) {
+            const uint32_t i = i0 + u * blockDim.x;
+            if (i >= m) break;
+            base[s.o + i] = v[u];
+        }
+    }
+    fence_proxy_async_smem();  // these reads of D come before the next bulk copy into it
+    __syncthreads();
+    return true;
+}
+
 template <int W>
 __global__ void __launch_bounds__(kThreads, 1) small_kernel(SmallArgs args) {
     using T = typename Elem<W>::T;
@@ -604,6 +765,7 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(SmallArgs args) {
         const PhiloxKey key = make_key(ad.seed);
         uint16_t* P0 = reinterpret_cast<uint16_t*>(dyn);
         uint16_t* P1 = P0 + ((m + 7u) & ~7u);
+        if (leaf_by_index(args, s, W)) continue;  // leaf_kernel's
         T* D;
         bool bulk = false;  // D arrives through load_bar
         if (args.medium) {
@@ -623,51 +785,7 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(SmallArgs args) {
                 }
             }
         } else {
-            // the rotation's pieces: logical [0, nA) from physical o+eps.., [nA, m) from o..; each
-            // piece's 16-byte-aligned middle goes by bulk copy when its shared-memory start is
-            // aligned too (the larger piece fixes D's shift), the rest by the threads
-            const uint32_t q = W >= 16 ? 1u : 16u / W;  // elements per 16 bytes
-            const uint32_t nA = m - s.eps;
-            const uintptr_t gA = reinterpret_cast<uintptr_t>(base + s.o + s.eps);
-            const uintptr_t gB = reinterpret_cast<uintptr_t>(base + s.o);
-            auto first_aligned = [&](uint32_t L0, uint32_t L1, uintptr_t g) -> uint32_t {
-                return min(L1, L0 + (uint32_t)(((16u - (g & 15u)) & 15u) / W));
-            };
-            const uint32_t fa = first_aligned(0u, nA, gA), fb = first_aligned(nA, m, gB);
-            const uint32_t dshift = nA >= s.eps ? (q - fa % q) % q : (q - fb % q) % q;
-            D = reinterpret_cast<T*>(P1 + ((m + 7u) & ~7u)) + dshift;
-            auto bulk_range = [&](uint32_t L0, uint32_t L1, uintptr_t g, uint32_t f, uint32_t& lo, uint32_t& hi) {
-                lo = hi = L0;
-                const uint32_t e = f + (L1 - f) / q * q;
-                if (e > f && ((g + (uintptr_t)(f - L0) * W) & 15u) == 0 && (dshift + f) % q == 0) {
-                    lo = f;
-                    hi = e;
-                }
-            };
-            uint32_t aLo, aHi, bLo, bHi;
-            bulk_range(0u, nA, gA, fa, aLo, aHi);
-            bulk_range(nA, m, gB, fb, bLo, bHi);
-            if (bLo == bHi) bLo = bHi = m;
-            if (tid == 0) {
-                const uint32_t bytes = (aHi - aLo + bHi - bLo) * (uint32_t)W;
-                if (bytes) {
-                    mbar_arrive_expect_tx(&sh.load_bar, bytes);
-                    auto issue = [&](uint32_t lo, uint32_t hi, uintptr_t g, uint32_t L0) {
-                        const char* src = reinterpret_cast<const char*>(g + (uintptr_t)(lo - L0) * W);
-                        char* dst = reinterpret_cast<char*>(D + lo);
-                        const uint32_t nbytes = (hi - lo) * (uint32_t)W;
-                        for (uint32_t off = 0; off < nbytes; off += 32768u)
-                            bulk_g2s(dst + off, src + off, min(32768u, nbytes - off), &sh.load_bar);
-                    };
-                    if (aHi > aLo) issue(aLo, aHi, gA, 0u);
-                    if (bHi > bLo) issue(bLo, bHi, gB, nA);
-                } else {
-                    mbar_arrive(&sh.load_bar);
-                }
-            }
-            for (uint32_t i = tid; i < aLo; i += blockDim.x) D[i] = base[phys_index(s, i)];
-            for (uint32_t i = aHi + tid; i < bLo; i += blockDim.x) D[i] = base[phys_index(s, i)];
-            for (uint32_t i = bHi + tid; i < m; i += blockDim.x) D[i] = base[phys_index(s, i)];
+            D = load_smem<W>(s, base, m, P1, &sh.load_bar);
             bulk = true;  // the phase completes either way
         }
         if (tid == 0) sh.stack_top = 0;
@@ -690,8 +808,8 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(SmallArgs args) {
                 // 32-bit reservations after D when they fit, else 16-bit ones in P0's place
                 const uint64_t mr = (m + 7u) & ~7u;
                 const uint64_t r32_off = 4 * mr + (args.medium ? 0 : (uint64_t)W * mr + 16);
-                if (r32_off + 4 * mr <= args.dyn_bytes)
-                    fy_parallel_data(D, P1, reinterpret_cast<uint32_t*>(dyn + r32_off), m, args.status);
+                if (r32_off + 4 * mr <= args.dyn_bytes)  // stamped: nothing cleared between rounds
+                    fy_parallel_stamped(D, P1, reinterpret_cast<uint32_t*>(dyn + r32_off), m, args.status);
                 else
                     fy_parallel_data(D, P1, P0, m, args.status);
                 in_place = true;
@@ -762,6 +880,46 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(SmallArgs args) {
     }
 }
 
+// The leaves small_kernel skips (leaf_by_index), from the same list with the same shared memory.
+template <int W>
+__global__ void __launch_bounds__(kThreads, 1) leaf_kernel(SmallArgs args) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmallShared& sh = *reinterpret_cast<SmallShared*>(smem_raw);
+    unsigned char* dyn = smem_raw + ((sizeof(SmallShared) + 15) & ~size_t(15));
+    if (block_call_failed(args.status)) return;
+    const uint32_t count = min(*args.count, args.capacity);
+    if (threadIdx.x == 0) {
+        mbar_init(&sh.load_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t loads = 0;
+    // the list is scanned kSmallStack entries per CTA and pass, one per thread; this CTA's matches
+    // are queued in the (here unused) stack and processed by the whole CTA
+    uint32_t* queue = reinterpret_cast<uint32_t*>(sh.stack);
+    for (uint32_t first = blockIdx.x * kSmallStack; first < count; first += gridDim.x * kSmallStack) {
+        if (threadIdx.x == 0) sh.stack_top = 0;
+        __syncthreads();
+        const uint32_t i = first + threadIdx.x;
+        if (threadIdx.x < kSmallStack && i < count && leaf_by_index(args, args.list[i], W))
+            queue[atomicAdd(&sh.stack_top, 1u)] = i;
+        __syncthreads();
+        const uint32_t nq = sh.stack_top;
+        bool ok = true;
+        for (uint32_t q = 0; q < nq && ok; ++q) {
+            const uint32_t item = queue[q];
+            const Sub s = args.list[item];
+            const ArrayDesc ad = args.arrays[s.arr];
+            auto* base = reinterpret_cast<typename Elem<W>::T*>(ad.data);
+            ok = fy_leaf_by_index<W>(args, s, base, (uint32_t)s.m, make_key(ad.seed), dyn, &sh.load_bar,
+                                     loads & 1u, item);
+            ++loads;
+        }
+        if (!ok) break;
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 size_t small_fixed_smem() { return (sizeof(SmallShared) + 15) & ~size_t(15); }
@@ -775,22 +933,44 @@ cudaError_t launch_small(const SmallArgs& args_in, uint32_t w, size_t smem, uint
     cudaError_t err;
     SmallArgs args = args_in;
     args.dyn_bytes = (uint32_t)(smem - small_fixed_smem());
-    ProfScope p(args.medium ? "solve_medium" : "solve_small", stream);
+    {
+        ProfScope p(args.medium ? "solve_medium" : "solve_small", stream);
+        switch (w) {
+            case 4:
+                err = ensure_dyn_smem(reinterpret_cast<const void*>(small_kernel<4>), (int)smem);
+                if (err != cudaSuccess) return err;
+                small_kernel<4><<<grid, kThreads, smem, stream>>>(args);
+                break;
+            case 8:
+                err = ensure_dyn_smem(reinterpret_cast<const void*>(small_kernel<8>), (int)smem);
+                if (err != cudaSuccess) return err;
+                small_kernel<8><<<grid, kThreads, smem, stream>>>(args);
+                break;
+            default:
+                err = ensure_dyn_smem(reinterpret_cast<const void*>(small_kernel<16>), (int)smem);
+                if (err != cudaSuccess) return err;
+                small_kernel<16><<<grid, kThreads, smem, stream>>>(args);
+                break;
+        }
+        err = cudaGetLastError();
+    }
+    if (err != cudaSuccess || args.medium) return err;
+    ProfScope pl("solve_leaf", stream);
     switch (w) {
         case 4:
-            err = ensure_dyn_smem(reinterpret_cast<const void*>(small_kernel<4>), (int)smem);
+            err = ensure_dyn_smem(reinterpret_cast<const void*>(leaf_kernel<4>), (int)smem);
             if (err != cudaSuccess) return err;
-            small_kernel<4><<<grid, kThreads, smem, stream>>>(args);
+            leaf_kernel<4><<<grid, kThreads, smem, stream>>>(args);
             break;
         case 8:
-            err = ensure_dyn_smem(reinterpret_cast<const void*>(small_kernel<8>), (int)smem);
+            err = ensure_dyn_smem(reinterpret_cast<const void*>(leaf_kernel<8>), (int)smem);
             if (err != cudaSuccess) return err;
-            small_kernel<8><<<grid, kThreads, smem, stream>>>(args);
+            leaf_kernel<8><<<grid, kThreads, smem, stream>>>(args);
             break;
         default:
-            err = ensure_dyn_smem(reinterpret_cast<const void*>(small_kernel<16>), (int)smem);
+            err = ensure_dyn_smem(reinterpret_cast<const void*>(leaf_kernel<16>), (int)smem);
             if (err != cudaSuccess) return err;
-            small_kernel<16><<<grid, kThreads, smem, stream>>>(args);
+            leaf_kernel<16><<<grid, kThreads, smem, stream>>>(args);
             break;
     }
     return cudaGetLastError();

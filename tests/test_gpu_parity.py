@@ -69,6 +69,14 @@ def test_fisher_yates_only(n, w):
     check(n, w, FY, seed=5)
 
 
+@pytest.mark.parametrize("n,w", [(24000, 4), (16000, 8), (16384, 8), (10000, 16)])
+def test_fisher_yates_leaves_on_indices(n, w):
+    """Leaves whose 32-bit reservations do not fit beside their data in shared memory: the steps
+    run on 16-bit indices, then the data are gathered (the near-capacity plan's 16K-element
+    leaves of 8-byte elements take this path)."""
+    check(n, w, FY, seed=9)
+
+
 @pytest.mark.parametrize("n,w", [(5000, 4), (5000, 8), (3000, 16), (17000, 8), (25000, 4)])
 def test_scatter_inside_one_sm(n, w):
     check(n, w, SMEM1, seed=2)
