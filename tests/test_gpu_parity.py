@@ -310,3 +310,22 @@ def test_batched_ex_per_array_seeds_match_the_oracle(with_plans):
             want = oracle.shuffle(a, seeds[i], p)
             assert np.array_equal(_from_dev(t, a), want), (w, i, sizes[i])
 
+
+
+def test_managed_workspace_calls_on_two_streams_are_ordered():
+    """Calls without a workspace share the library's managed one: issued back to back on two
+    streams, the second is ordered after the first on the device, and both give the oracle's
+    output (a larger second call also regrows the workspace safely)."""
+    rip.rip_release_workspace()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    cases = [(1 << 20, 4, INPLACE1, 31, s1), (3 << 19, 8, INPLACE2, 32, s2), (1 << 21, 8, INPLACE2, 33, s1),
+             (300_000, 16, rip.Plan(ks=[32], Ts=[4096], Bs=[128], base=1000), 34, s2)]
+    arrays = [_make(n, w) for n, w, _, _, _ in cases]
+    ts = [_to_dev(a) for a in arrays]
+    torch.cuda.synchronize()
+    for t, (n, w, plan, seed, st) in zip(ts, cases):
+        rip.shuffle_(t, seed, plan=plan, stream=st)
+    torch.cuda.synchronize()
+    assert rip.rip_get_device_status(0) == rip.RIP_OK
+    for t, a, (n, w, plan, seed, _) in zip(ts, arrays, cases):
+        assert np.array_equal(_from_dev(t, a), oracle.shuffle(a, seed, _oplan(plan))), (n, w)
