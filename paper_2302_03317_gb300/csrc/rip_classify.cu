@@ -10,20 +10,22 @@
 // the tile's tail for that bucket and goes to the pool at the end of the tile.
 //
 // Per round of nwr*128 consecutive positions:
-//   load     the round's elements arrive in a shared-memory buffer by a bulk
-//            (TMA) copy one or two rounds ahead, completing on an mbarrier;
+//   load     the round's elements arrive in a shared-memory buffer by bulk
+//            (TMA) copies one or two rounds ahead, completing on an mbarrier;
 //            ragged edges (unaligned ends, the rotation's wrap piece) are
-//            copied by the threads
+//            copied by the threads.  The I/O warp does nothing else: with the
+//            chunk stores also on the copy engine, a round's load queued behind
+//            them and the compute warps waited for their input
 //   rank     Philox bucket draws (a1), stable ranks per bucket: the lanes of a
 //            step with the same bucket come from a 32-entry shared-memory mask
 //            row per warp (indexed by the low five bucket bits) and one ballot
 //            per higher bit; the warp's running count per bucket lives in a
 //            (bucket, warp) table of 16-bit counters (a2)
-//            -- meanwhile the chunks completed by the previous round are
-//               written out, so stores overlap the arithmetic
 //   book     per bucket: exclusive prefix over the ranking warps (one lane
 //            per bucket, 32 buckets per warp), blocks completed, home slots or
 //            pool blocks for blocks that receive data, slot words
+//            -- meanwhile the other warps write the chunks completed by the
+//               previous round to their blocks with 16-byte stores
 //   place    every element goes to its bucket's shared-memory chunk (Bs
 //            elements, Bs divides B), straight to its block in global memory
 //            when its whole chunk lies inside this round, or is carried into
@@ -41,12 +43,17 @@ namespace rip {
 
 namespace {
 
+template <bool V>
+struct BoolC {
+    static constexpr bool value = V;
+};
+
 constexpr uint64_t kLocPool = 1ull << 63;  // location in the pool (else: element index in the array)
 constexpr uint32_t kNone = 0xffffffffu;
+constexpr uint32_t kLoadPiece = 4096u;  // bytes per bulk copy of a round's input (a multiple of 16)
 
 struct ClsMisc {
     uint64_t full[3];      // input buffer loaded (transaction count of the bulk copy)
-    uint64_t stage_free;   // the I/O warp has read out the chunks completed by the previous round
     uint64_t flush_ready;  // the compute warps have placed a round
     uint64_t pool_base;
     uint32_t tile;
@@ -147,16 +154,15 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
     for (uint32_t j = tid; j < nwr * 32u; j += blockDim.x) masks[j] = 0;  // kept zero after every step
     if (tid == 0) {
         for (uint32_t i = 0; i < nbuf; ++i) mbar_init(&ms.full[i], 1);
-        mbar_init(&ms.stage_free, 1);
         mbar_init(&ms.flush_ready, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         ms.fail = 0;
     }
     __syncthreads();
 
-    // completions so far of: the input buffers (one per round), stage_free (one per round and
-    // one per tile), flush_ready (one per round); every thread counts the same way
-    uint32_t grc = 0, sfc = 0, frc = 0;
+    // completions so far of the input buffers and of flush_ready (one each per round); every
+    // thread counts the same way
+    uint32_t grc = 0, frc = 0;
     for (;;) {
         if (tid == 0) {
             const uint32_t c = atomicAdd(&a.counters[1], 1u);
@@ -244,21 +250,23 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                 for (uint32_t e = b_hi + lane; e < e_hi; e += 32u)
                     buf[(uint32_t)((int64_t)e - e0) + sh] = e < avail ? base[alo + e] : base[phys_index(Sp, lo + e)];
                 __syncwarp();
-                if (lane == 0) {
-                    if (b_hi > b_lo) {
-                        const uint32_t bytes = (b_hi - b_lo) * (uint32_t)W;
-                        mbar_arrive_expect_tx(&ms.full[gr % nbuf], bytes);
-                        bulk_g2s(buf + ((uint32_t)((int64_t)b_lo - e0) + sh), base + alo + b_lo, bytes,
-                                 &ms.full[gr % nbuf]);
-                    } else {
-                        mbar_arrive(&ms.full[gr % nbuf]);
-                    }
+                if (b_hi > b_lo) {
+                    // pieces of kLoadPiece bytes, one per lane: several copies in flight fetch a round
+                    // sooner than one long copy
+                    const uint32_t bytes = (b_hi - b_lo) * (uint32_t)W;
+                    if (lane == 0) mbar_arrive_expect_tx(&ms.full[gr % nbuf], bytes);
+                    __syncwarp();
+                    unsigned char* d0 = reinterpret_cast<unsigned char*>(buf + ((uint32_t)((int64_t)b_lo - e0) + sh));
+                    const unsigned char* s0 = reinterpret_cast<const unsigned char*>(base + alo + b_lo);
+                    for (uint32_t off = lane * kLoadPiece; off < bytes; off += 32u * kLoadPiece)
+                        bulk_g2s(d0 + off, s0 + off, min(kLoadPiece, bytes - off), &ms.full[gr % nbuf]);
+                } else if (lane == 0) {
+                    mbar_arrive(&ms.full[gr % nbuf]);
                 }
             };
             for (uint32_t rr = 0; rr + 1 < nbuf && rr < nrounds; ++rr) load(rr);
-            if (lane == 0) mbar_arrive(&ms.stage_free);  // round 0 may place: nothing to flush yet
             for (uint32_t rr = 0; rr < nrounds; ++rr) {
-                // round rr is placed: its chunks and flush list are ready, the buffer of rr-1 is free
+                // round rr is placed: the buffer of round rr-1 is free (its carried elements are placed)
                 // (lane 0 decides for the warp: its wait, or a failure the compute warps recorded)
                 uint32_t ok = 1;
                 if (lane == 0) {
@@ -274,44 +282,10 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                 __syncwarp();  // lane 0's acquire covers the whole warp
                 if (!ok) break;
                 if (rr + nbuf - 1 < nrounds) load(rr + nbuf - 1);
-                const uint32_t par = rr & 1u;
-                const uint32_t nf = ms.nflush[par];
-                const uint64_t* fl = flist + par * k;
-                bool issued = false;
-                if (flush_vec) {
-                    for (uint32_t f = lane; f < nf; f += 32u) {
-                        const uint64_t e = fl[f];
-                        const uint32_t b = (uint32_t)(e >> 48) & 0x3FFu;
-                        const uint64_t loc = e & kEntLoc;
-                        if ((loc & kLocPool) && (loc & ~kLocPool) + Bs > a.pool_cap) continue;  // reported
-                        bulk_s2g(loc_ptr(loc), stage + (size_t)b * Bs, Bs * (uint32_t)W);
-                        issued = true;
-                    }
-                    if (issued) {
-                        bulk_commit();
-                        bulk_wait_read();
-                    }
-                    if (rr + 1 == nrounds) {  // the tails read open blocks back: every store is complete
-                        bulk_wait_all();
-                        fence_proxy_async_global();
-                    }
-                } else {
-                    for (uint32_t f = 0; f < nf; ++f) {
-                        const uint64_t e = fl[f];
-                        const uint32_t b = (uint32_t)(e >> 48) & 0x3FFu;
-                        const uint64_t loc = e & kEntLoc;
-                        if ((loc & kLocPool) && (loc & ~kLocPool) + Bs > a.pool_cap) continue;  // reported
-                        T* dst = loc_ptr(loc);
-                        const T* src = stage + (size_t)b * Bs;
-                        for (uint32_t u = lane; u < Bs; u += 32u) dst[u] = src[u];
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&ms.stage_free);  // the chunks are read out: round rr+1 may place
             }
             // after a failure: the loads still in flight land in this CTA's shared memory, so they
             // complete before the CTA leaves (the last load of each buffer; earlier ones were
-            // consumed); stores issued by this warp have read their sources already
+            // consumed)
             if (ms.fail && lane == 0) {
                 for (uint32_t j = loads_issued > nbuf ? loads_issued - nbuf : 0u; j < loads_issued; ++j) {
                     const uint32_t gr = grc + j;
@@ -321,6 +295,43 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
             __syncwarp();
         } else {
             // ---------------------------------------------------------------- compute warps
+            // the chunks that round pp's bookkeeping listed as complete go to their blocks, 16 bytes
+            // (or one element) per thread, spread over many warps instead of queueing behind one
+            // copy engine; the warps that do the bookkeeping (one lane per bucket, on the round's
+            // critical path) take no share when others are left
+            const uint32_t fw0 = k < kComputeThreads ? k / 32u : 0u;  // first flushing warp
+            const uint32_t fth = kComputeThreads - fw0 * 32u;          // flushing threads
+            const uint32_t ftid = tid - fw0 * 32u;                     // (wraps for the others)
+            auto flush_chunks = [&](uint32_t pp) {
+                if (warp < fw0) return;
+                const uint32_t nf = ms.nflush[pp];
+                const uint64_t* fl = flist + pp * k;
+                if (flush_vec) {
+                    const uint32_t vpc = Bs * (uint32_t)W / 16u;  // 16-byte words per chunk
+                    const bool vpc_pow2 = (vpc & (vpc - 1u)) == 0;
+                    const uint32_t vsh = log2_pow2(vpc);
+                    for (uint32_t i = ftid; i < nf * vpc; i += fth) {
+                        const uint32_t f = vpc_pow2 ? i >> vsh : i / vpc;
+                        const uint32_t u = i - f * vpc;
+                        const uint64_t e = fl[f];
+                        const uint32_t b = (uint32_t)(e >> 48) & 0x3FFu;
+                        const uint64_t loc = e & kEntLoc;
+                        if ((loc & kLocPool) && (loc & ~kLocPool) + Bs > a.pool_cap) continue;  // reported
+                        reinterpret_cast<uint4*>(loc_ptr(loc))[u] =
+                            reinterpret_cast<const uint4*>(stage + (size_t)b * Bs)[u];
+                    }
+                } else {
+                    for (uint32_t i = ftid; i < nf * Bs; i += fth) {
+                        const uint32_t f = bs_pow2 ? i >> bs_shift : i / Bs;
+                        const uint32_t u = i - f * Bs;
+                        const uint64_t e = fl[f];
+                        const uint32_t b = (uint32_t)(e >> 48) & 0x3FFu;
+                        const uint64_t loc = e & kEntLoc;
+                        if ((loc & kLocPool) && (loc & ~kLocPool) + Bs > a.pool_cap) continue;  // reported
+                        loc_ptr(loc)[u] = stage[(size_t)b * Bs + u];
+                    }
+                }
+            };
             for (uint32_t rr = 0; rr < nrounds; ++rr) {
                 const uint32_t R = rr * round;
                 const uint32_t gr = grc + rr;
@@ -330,14 +341,15 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                 // rank: lanes of a step with the same bucket read the warp's running count
                 // together, the lowest of them writes it back advanced by their number
                 uint32_t packed[4] = {kNone, kNone, kNone, kNone};
-                if (warp < nwr) {
+                // IN: every position of the round is valid (all rounds but a tile's first and last)
+                auto rank4 = [&](auto in_c) {
+                    constexpr bool IN = decltype(in_c)::value;
                     const uint4 words = group_philox(pk, L, Sp.o, Q0 + (R >> 2) + warp * 32u);
                     const uint32_t v0 = R + warp * 128u + lane;
-                    const bool interior = R >= delta && R + round <= rv;  // every position is valid
 #pragma unroll
                     for (uint32_t s = 0; s < 4; ++s) {
                         const uint32_t v = v0 + 32u * s;
-                        const bool valid = interior || (v >= delta && v - delta < r);
+                        const bool valid = IN || (v >= delta && v - delta < r);
                         const uint32_t b = bucket_of(group_step_word(words, s), k);
                         // lanes with the same bucket: the low five bits through the warp's mask
                         // row (one shared atomic OR per lane), the higher ones by ballot -- on
@@ -357,8 +369,17 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                         __syncwarp();
                         if (valid) packed[s] = b | ((pre + (uint32_t)__popc(peers & lt_mask)) << 10);
                     }
+                };
+                if (warp < nwr) {
+                    if (R >= delta && R + round <= rv)
+                        rank4(BoolC<true>{});
+                    else
+                        rank4(BoolC<false>{});
                 }
                 compute_sync();  // A
+                // the previous round's completed chunks leave the stage before this round places
+                // (barrier B lies between), while the bookkeeping warps work
+                if (rr > 0) flush_chunks(par ^ 1u);
 
                 // bookkeeping: one lane per bucket; the (bucket, warp) counts become offsets from
                 // the start of the bucket's current chunk (below Bs: the staged chunk)
@@ -504,13 +525,10 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                         }
                     }
                 }
-                // this round's input is loaded and the previous round's chunks are read out
+                // this round's input is loaded
                 if (tid == 0) {
                     if (!mbar_wait(&ms.full[gr % nbuf], (gr / nbuf) & 1u, polls)) {
                         report(a.status, RIP_ETIMEOUT, 0x6207, gr);
-                        ms.fail = 1;
-                    } else if (!mbar_wait(&ms.stage_free, (sfc + rr) & 1u, polls)) {
-                        report(a.status, RIP_ETIMEOUT, 0x6209, gr);
                         ms.fail = 1;
                     }
                     ms.cfail = ms.fail;  // one verdict for all compute warps (ms.fail may change later)
@@ -569,7 +587,6 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                     }
                 }
                 carried_buf = gr % nbuf;
-                if (flush_vec) fence_proxy_async_smem();  // staged elements are read by bulk stores
                 // the warp's column of the table is read only by the warp itself: clear it
                 __syncwarp();
                 if (warp < nwr)
@@ -577,13 +594,10 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                 compute_sync();  // C
                 if (tid == 0) mbar_arrive(&ms.flush_ready);
             }
-            // end of the tile: the last chunks are read out, then the carried elements
-            // (ms.cfail is the verdict every compute thread saw at the last barrier B)
+            // end of the tile: the last round's chunks go out, then the carried elements take the
+            // stage (ms.cfail is the verdict every compute thread saw at the last barrier B)
             if (!ms.cfail) {
-                if (tid == 0 && !mbar_wait(&ms.stage_free, (sfc + nrounds) & 1u, polls)) {
-                    report(a.status, RIP_ETIMEOUT, 0x620A, nrounds);
-                    ms.fail = 1;
-                }
+                if (nrounds > 0) flush_chunks((nrounds - 1u) & 1u);
                 compute_sync();
                 const T* cb = bufs + (size_t)carried_buf * g.bufstride;
 #pragma unroll
@@ -596,7 +610,6 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
             }
         }
         grc += nrounds;
-        sfc += nrounds + 1u;
         frc += nrounds;
         __syncthreads();
         if (ms.fail) break;  // a copy or a hand-off did not arrive: reported, the level's output is void
