@@ -31,6 +31,15 @@
 //            when its whole chunk lies inside this round, or is carried into
 //            the next round when it starts a chunk that completes later
 //
+// Pipelined rounds (k = 64 or 256 with 4- or 8-byte elements, the common
+// plans): the k/32 bookkeeping warps do nothing else, and book round i-1 while
+// the other warps write out round i-2's completed chunks and rank round i; the
+// rank warps then place round i-1.  The (bucket, warp) table has two copies, so
+// round i's counts do not disturb round i-1's offsets; elements carried into
+// the next round wait in registers, so a round's buffer is free as soon as it
+// is placed.  With one barrier per phase the bookkeeping (latency-bound, k
+// lanes) hides behind the ranking (throughput-bound) instead of following it.
+//
 // A block gets its location when its first chunk is written.  A home slot h
 // may be used once the tile's elements [0, (h+1)B) have been read; otherwise
 // (at the start of a tile, when chunks are smaller than blocks) the block goes
@@ -96,8 +105,13 @@ constexpr uint32_t kComputeThreads = kIoWarp * 32u;
 // ranks with 16 warps, not 8: rounds of 2048 positions halve the per-element share of the
 // bookkeeping over 1024 buckets (measured at 2^34: classify 1.42 -> 1.19 s for u32, 2.20 -> 1.78 s
 // for u64; 31 warps measured slower, its staged chunks shrink to 32 or 16 bytes)
+// Pipelined rounds (k = 64 or 256, elements of 4 or 8 bytes): warps 0 .. k/32-1 do the
+// bookkeeping only, the others rank and place, and the bookkeeping of a round runs while the next
+// round is ranked (the table of counts is double-buffered).
+__host__ __device__ constexpr bool cls_pipe(uint32_t k, uint32_t w) { return (k == 64u || k == 256u) && w <= 8u; }
 __host__ __device__ constexpr uint32_t cls_nwr(uint32_t k, uint32_t w) {
-    return (k >= 1024u ? 16384u / k : 8192u / k) < (w >= 16 ? 16u : kIoWarp)
+    return cls_pipe(k, w) ? kIoWarp - k / 32u
+           : (k >= 1024u ? 16384u / k : 8192u / k) < (w >= 16 ? 16u : kIoWarp)
                ? (k >= 1024u ? 16384u / k : 8192u / k)
                : (w >= 16 ? 16u : kIoWarp);
 }
@@ -117,6 +131,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const ClsCfg g = a.cls;
     constexpr uint32_t KC = KB > 0 ? (1u << KB) : 0u;
+    constexpr bool PIPE = KB > 0 && cls_pipe(KC, W);
     ClsMisc& ms = *reinterpret_cast<ClsMisc*>(smem_raw);
     uint16_t* tbl = reinterpret_cast<uint16_t*>(smem_raw + g.off_tbl);
     uint32_t* run = reinterpret_cast<uint32_t*>(smem_raw + g.off_u32);
@@ -204,7 +219,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
         }
         // every home slot starts empty; completed blocks fill in their words
         for (uint32_t h = tid; h < H; h += blockDim.x) a.words[hs0 + h] = 0u;
-        for (uint32_t j = tid; j < k * S; j += blockDim.x) tbl[j] = 0;
+        for (uint32_t j = tid; j < k * S * (PIPE ? 2u : 1u); j += blockDim.x) tbl[j] = 0;
         if (tid == 0) {
             ms.home_next = 0;
             ms.nflush[0] = ms.nflush[1] = 0;
@@ -222,6 +237,191 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
         uint32_t carried[4] = {kNone, kNone, kNone, kNone};
         uint32_t carried_buf = 0;  // buffer of the carried elements
         uint32_t loads_issued = 0;  // I/O warp: rounds whose load has been issued
+
+            // bookkeeping of round q: one lane per bucket; the (bucket, warp) counts in tb become
+            // offsets from the start of the bucket's current chunk (below Bs: the staged chunk)
+            auto book = [&](uint32_t q, uint16_t* tb) {
+                const uint32_t R = q * round;
+                const uint32_t par = q & 1u;
+                const int64_t e_rd = (int64_t)R + round - delta;  // elements read through this round
+                const uint32_t e_end = min(e_rd < (int64_t)r ? (uint32_t)e_rd : r, avail);
+                const uint32_t F = min(H, b_pow2 ? e_end >> b_shift : a.fdB.div(e_end));
+                for (uint32_t b0 = warp * 32u; b0 < k; b0 += kComputeThreads) {
+                    const uint32_t b = b0 + lane;
+                    const bool mine = b < k;
+                    const uint32_t cur = mine ? run[b] : 0u;
+                    const uint32_t fill = bs_pow2 ? cur & (Bs - 1u) : cur % Bs;
+                    uint32_t acc = fill;
+                    if (mine) {
+                        uint16_t* col = tb + b * S;
+                        if constexpr (KB > 0) {
+                            // loads first, in batches of eight: the stores cannot alias them,
+                            // but the compiler cannot tell, and would wait for each load in turn
+                            constexpr uint32_t NW = cls_nwr(KC, W);
+#pragma unroll
+                            for (uint32_t j0 = 0; j0 < NW; j0 += 8) {
+                                uint32_t cv[8];
+#pragma unroll
+                                for (uint32_t j = 0; j < 8; ++j)
+                                    if (j0 + j < NW) cv[j] = col[j0 + j];
+#pragma unroll
+                                for (uint32_t j = 0; j < 8; ++j)
+                                    if (j0 + j < NW) {
+                                        col[j0 + j] = (uint16_t)acc;
+                                        acc += cv[j];
+                                    }
+                            }
+                        } else {
+                            for (uint32_t j = 0; j < nwr; ++j) {
+                                const uint32_t c = col[j];
+                                col[j] = (uint16_t)acc;
+                                acc += c;
+                            }
+                        }
+                    }
+                    const uint32_t t = acc - fill, nr = cur + t;
+                    const uint32_t c0 = bs_pow2 ? cur >> bs_shift : cur / Bs;
+                    const uint32_t c1 = bs_pow2 ? nr >> bs_shift : nr / Bs;
+                    const bool moves = mine && c1 > c0;  // a chunk completes: blocks receive data
+                    uint32_t jlo = 0, jhi = 0, ob = kNone, jn = 0, nb = 0;
+                    uint64_t oloc = 0;
+                    if (moves) {
+                        jlo = c0 / cpb;
+                        jhi = (c1 - 1u) / cpb;
+                        ob = oblk[b];
+                        oloc = optr[b];
+                        jn = ob == jlo ? jlo + 1u : jlo;
+                        nb = jhi + 1u - jn;
+                    }
+                    uint32_t ex = nb;
+#pragma unroll
+                    for (uint32_t d = 1; d < 32u; d <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, ex, d);
+                        if (lane >= d) ex += y;
+                    }
+                    const uint32_t wtotal = __shfl_sync(0xffffffffu, ex, 31);
+                    ex -= nb;
+                    // whole blocks staged: completed blocks never outrun the read elements, so
+                    // the frontier binds only past H (wrap piece) and a plain add is exact;
+                    // chunks: a block is placed at its first chunk, so claim no slot past F
+                    uint32_t hb0 = 0, lim = F;
+                    if (lane == 0 && wtotal) {
+                        if (cpb == 1) {
+                            hb0 = atomicAdd(&ms.home_next, wtotal);
+                        } else {
+                            uint32_t old = *reinterpret_cast<volatile uint32_t*>(&ms.home_next), tk = 0;
+                            for (;;) {
+                                tk = old < F ? min(wtotal, F - old) : 0u;
+                                if (tk == 0) break;
+                                const uint32_t prev = atomicCAS(&ms.home_next, old, old + tk);
+                                if (prev == old) break;
+                                old = prev;
+                            }
+                            hb0 = old;
+                            lim = old + tk;
+                        }
+                    }
+                    hb0 = __shfl_sync(0xffffffffu, hb0, 0);
+                    lim = __shfl_sync(0xffffffffu, lim, 0);
+                    const unsigned fl_mask = __ballot_sync(0xffffffffu, moves);
+                    uint32_t fl0 = 0;
+                    if (lane == 0 && fl_mask) fl0 = atomicAdd(&ms.nflush[par], (uint32_t)__popc(fl_mask));
+                    fl0 = __shfl_sync(0xffffffffu, fl0, 0);
+                    if (mine && t) {
+                        rb[b] = cur;
+                        run[b] = nr;
+                    }
+                    if (moves) {
+                        const uint32_t hb = hb0 + ex;
+                        const uint32_t tk = lim > hb ? min(nb, lim - hb) : 0u;
+                        uint64_t pb = 0;
+                        if (nb > tk) {
+                            const uint64_t need = (uint64_t)(nb - tk) * B;
+                            const uint64_t alloc = (need + a.pool_align - 1) / a.pool_align * a.pool_align;
+                            pb = atomicAdd((unsigned long long*)a.pool_used, (unsigned long long)alloc);
+                            if (pb + need > a.pool_cap) report(a.status, RIP_EWORKSPACE, 0x6202, pb);
+                        }
+                        jnew[b] = jn;
+                        take[b] = tk;
+                        hbase[b] = hb;
+                        pbase[b] = pb;
+                        auto locf = [&](uint32_t j) -> uint64_t {
+                            if (j == ob) return oloc;
+                            const uint32_t x = j - jn;
+                            if (x < tk) return alo + (uint64_t)(hb + x) * B;
+                            return kLocPool | (pb + (uint64_t)(x - tk) * B);
+                        };
+                        const uint64_t l0 = locf(jlo);
+                        jloc[b] = l0;
+                        // the staged chunk c0 completes: its flush entry
+                        flist[par * k + fl0 + (uint32_t)__popc(fl_mask & lt_mask)] =
+                            (l0 + (uint64_t)(c0 % cpb) * Bs) | ((uint64_t)b << 48);
+                        // blocks completed this round: slot words (home) or demoted records (pool)
+                        const uint32_t jc0 = b_pow2 ? cur >> b_shift : a.fdB.div(cur);
+                        const uint32_t jc1 = b_pow2 ? nr >> b_shift : a.fdB.div(nr);
+                        for (uint32_t j = jc0; j < jc1; ++j) {
+                            if (j >= (1u << kBlkBits)) report(a.status, RIP_EINVAL, 0x6203, j);
+                            const uint64_t l = locf(j);
+                            if (!(l & kLocPool)) {
+                                const uint32_t h = b_pow2 ? (uint32_t)((l - alo) >> b_shift)
+                                                          : a.fdB.div((uint32_t)(l - alo));
+                                a.words[hs0 + h] = kWordOcc | (b << kBlkBits) | j;
+                            } else {
+                                if ((l & ~kLocPool) + B > a.pool_cap) continue;  // allocation failure, reported
+                                const uint32_t rec = atomicAdd(&a.counters[2], 1u);
+                                if (rec < a.dem_cap)
+                                    a.dem[rec] = DemRec{tr.sp, tile, b, j, l & ~kLocPool};
+                                else
+                                    report(a.status, RIP_EWORKSPACE, 0x6204, rec);
+                            }
+                        }
+                        if ((uint64_t)(jhi + 1u) * B > nr) {
+                            oblk[b] = jhi;
+                            optr[b] = locf(jhi);
+                        } else {
+                            oblk[b] = kNone;
+                        }
+                    }
+                }
+            };
+
+            // the chunks that round pp's bookkeeping listed as complete go to their blocks, 16 bytes
+            // (or one element) per thread, spread over many warps instead of queueing behind one
+            // copy engine; the warps that do the bookkeeping (one lane per bucket, on the round's
+            // critical path) take no share when others are left
+            const uint32_t fw0 = k < kComputeThreads ? k / 32u : 0u;  // first flushing warp
+            const uint32_t fth = kComputeThreads - fw0 * 32u;          // flushing threads
+            const uint32_t ftid = tid - fw0 * 32u;                     // (wraps for the others)
+            auto flush_chunks = [&](uint32_t pp) {
+                if (warp < fw0) return;
+                const uint32_t nf = ms.nflush[pp];
+                const uint64_t* fl = flist + pp * k;
+                if (flush_vec) {
+                    const uint32_t vpc = Bs * (uint32_t)W / 16u;  // 16-byte words per chunk
+                    const bool vpc_pow2 = (vpc & (vpc - 1u)) == 0;
+                    const uint32_t vsh = log2_pow2(vpc);
+                    for (uint32_t i = ftid; i < nf * vpc; i += fth) {
+                        const uint32_t f = vpc_pow2 ? i >> vsh : i / vpc;
+                        const uint32_t u = i - f * vpc;
+                        const uint64_t e = fl[f];
+                        const uint32_t b = (uint32_t)(e >> 48) & 0x3FFu;
+                        const uint64_t loc = e & kEntLoc;
+                        if ((loc & kLocPool) && (loc & ~kLocPool) + Bs > a.pool_cap) continue;  // reported
+                        reinterpret_cast<uint4*>(loc_ptr(loc))[u] =
+                            reinterpret_cast<const uint4*>(stage + (size_t)b * Bs)[u];
+                    }
+                } else {
+                    for (uint32_t i = ftid; i < nf * Bs; i += fth) {
+                        const uint32_t f = bs_pow2 ? i >> bs_shift : i / Bs;
+                        const uint32_t u = i - f * Bs;
+                        const uint64_t e = fl[f];
+                        const uint32_t b = (uint32_t)(e >> 48) & 0x3FFu;
+                        const uint64_t loc = e & kEntLoc;
+                        if ((loc & kLocPool) && (loc & ~kLocPool) + Bs > a.pool_cap) continue;  // reported
+                        loc_ptr(loc)[u] = stage[(size_t)b * Bs + u];
+                    }
+                }
+            };
 
         if (io) {
             // ---------------------------------------------------------------- I/O warp
@@ -264,24 +464,48 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                     mbar_arrive(&ms.full[gr % nbuf]);
                 }
             };
-            for (uint32_t rr = 0; rr + 1 < nbuf && rr < nrounds; ++rr) load(rr);
-            for (uint32_t rr = 0; rr < nrounds; ++rr) {
-                // round rr is placed: the buffer of round rr-1 is free (its carried elements are placed)
-                // (lane 0 decides for the warp: its wait, or a failure the compute warps recorded)
-                uint32_t ok = 1;
-                if (lane == 0) {
-                    ok = mbar_wait(&ms.flush_ready, (frc + rr) & 1u, polls);
-                    if (!ok) {
-                        report(a.status, RIP_ETIMEOUT, 0x6208, rr);
-                        ms.fail = 1;
-                    } else if (ms.fail) {
-                        ok = 0;
+            if constexpr (PIPE) {
+                // pipelined rounds: after round rr is placed its buffer is free (the elements it
+                // carries into the next round wait in registers), so round rr + nbuf loads into it.
+                // (The chunk stores stay off this warp: a bulk copy issued after this thread's own
+                // global stores was measured to wait for them.)
+                for (uint32_t rr = 0; rr < nbuf && rr < nrounds; ++rr) load(rr);
+                for (uint32_t rr = 0; rr < nrounds; ++rr) {
+                    uint32_t ok = 1;
+                    if (lane == 0) {
+                        ok = mbar_wait(&ms.flush_ready, (frc + rr) & 1u, polls);
+                        if (!ok) {
+                            report(a.status, RIP_ETIMEOUT, 0x6208, rr);
+                            ms.fail = 1;
+                        } else if (ms.fail) {
+                            ok = 0;
+                        }
                     }
+                    ok = __shfl_sync(0xffffffffu, ok, 0);
+                    __syncwarp();  // lane 0's acquire covers the whole warp
+                    if (!ok) break;
+                    if (rr + nbuf < nrounds) load(rr + nbuf);
                 }
-                ok = __shfl_sync(0xffffffffu, ok, 0);
-                __syncwarp();  // lane 0's acquire covers the whole warp
-                if (!ok) break;
-                if (rr + nbuf - 1 < nrounds) load(rr + nbuf - 1);
+            } else {
+                for (uint32_t rr = 0; rr + 1 < nbuf && rr < nrounds; ++rr) load(rr);
+                for (uint32_t rr = 0; rr < nrounds; ++rr) {
+                    // round rr is placed: the buffer of round rr-1 is free (its carried elements are placed)
+                    // (lane 0 decides for the warp: its wait, or a failure the compute warps recorded)
+                    uint32_t ok = 1;
+                    if (lane == 0) {
+                        ok = mbar_wait(&ms.flush_ready, (frc + rr) & 1u, polls);
+                        if (!ok) {
+                            report(a.status, RIP_ETIMEOUT, 0x6208, rr);
+                            ms.fail = 1;
+                        } else if (ms.fail) {
+                            ok = 0;
+                        }
+                    }
+                    ok = __shfl_sync(0xffffffffu, ok, 0);
+                    __syncwarp();  // lane 0's acquire covers the whole warp
+                    if (!ok) break;
+                    if (rr + nbuf - 1 < nrounds) load(rr + nbuf - 1);
+                }
             }
             // after a failure: the loads still in flight land in this CTA's shared memory, so they
             // complete before the CTA leaves (the last load of each buffer; earlier ones were
@@ -293,45 +517,154 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                 }
             }
             __syncwarp();
-        } else {
-            // ---------------------------------------------------------------- compute warps
-            // the chunks that round pp's bookkeeping listed as complete go to their blocks, 16 bytes
-            // (or one element) per thread, spread over many warps instead of queueing behind one
-            // copy engine; the warps that do the bookkeeping (one lane per bucket, on the round's
-            // critical path) take no share when others are left
-            const uint32_t fw0 = k < kComputeThreads ? k / 32u : 0u;  // first flushing warp
-            const uint32_t fth = kComputeThreads - fw0 * 32u;          // flushing threads
-            const uint32_t ftid = tid - fw0 * 32u;                     // (wraps for the others)
-            auto flush_chunks = [&](uint32_t pp) {
-                if (warp < fw0) return;
-                const uint32_t nf = ms.nflush[pp];
-                const uint64_t* fl = flist + pp * k;
-                if (flush_vec) {
-                    const uint32_t vpc = Bs * (uint32_t)W / 16u;  // 16-byte words per chunk
-                    const bool vpc_pow2 = (vpc & (vpc - 1u)) == 0;
-                    const uint32_t vsh = log2_pow2(vpc);
-                    for (uint32_t i = ftid; i < nf * vpc; i += fth) {
-                        const uint32_t f = vpc_pow2 ? i >> vsh : i / vpc;
-                        const uint32_t u = i - f * vpc;
-                        const uint64_t e = fl[f];
-                        const uint32_t b = (uint32_t)(e >> 48) & 0x3FFu;
-                        const uint64_t loc = e & kEntLoc;
-                        if ((loc & kLocPool) && (loc & ~kLocPool) + Bs > a.pool_cap) continue;  // reported
-                        reinterpret_cast<uint4*>(loc_ptr(loc))[u] =
-                            reinterpret_cast<const uint4*>(stage + (size_t)b * Bs)[u];
+        } else if constexpr (PIPE) {
+            // ---------------------------------------------------------------- compute warps, pipelined
+            // iteration it: the rank warps rank round it while the bookkeeping warps book round it-1
+            // (barrier X); then the rank warps place round it-1 (barrier Y).  The table of counts
+            // alternates between two copies, so a round's offsets survive until it is placed.
+            constexpr uint32_t NB = KC / 32u;  // bookkeeping warps: one lane per bucket
+            const bool bookw = warp < NB;
+            const uint32_t rw = warp - NB;  // rank index of a rank warp
+            if (bookw) {
+                for (uint32_t it = 0; it <= nrounds; ++it) {
+                    if (it >= 1) book(it - 1, tbl + ((it - 1) & 1u) * k * S);
+                    // thread 0 (a bookkeeping thread): round it-1's input is loaded
+                    if (tid == 0) {
+                        if (it >= 1) {
+                            const uint32_t gq = grc + it - 1;
+                            if (!mbar_wait(&ms.full[gq % nbuf], (gq / nbuf) & 1u, polls)) {
+                                report(a.status, RIP_ETIMEOUT, 0x6207, gq);
+                                ms.fail = 1;
+                            }
+                        }
+                        ms.cfail = ms.fail;  // one verdict for all compute warps
                     }
-                } else {
-                    for (uint32_t i = ftid; i < nf * Bs; i += fth) {
-                        const uint32_t f = bs_pow2 ? i >> bs_shift : i / Bs;
-                        const uint32_t u = i - f * Bs;
-                        const uint64_t e = fl[f];
-                        const uint32_t b = (uint32_t)(e >> 48) & 0x3FFu;
-                        const uint64_t loc = e & kEntLoc;
-                        if ((loc & kLocPool) && (loc & ~kLocPool) + Bs > a.pool_cap) continue;  // reported
-                        loc_ptr(loc)[u] = stage[(size_t)b * Bs + u];
+                    compute_sync();  // X
+                    if (ms.cfail) {
+                        if (tid == 0) mbar_arrive(&ms.flush_ready);  // lets the I/O warp see the failure
+                        break;
+                    }
+                    // round it's flush list starts empty: the list of the same parity (round it-2)
+                    // was written out before barrier X
+                    if (tid == 0 && it < nrounds) ms.nflush[it & 1u] = 0;
+                    if (it >= 1) {
+                        compute_sync();  // Y
+                        if (tid == 0) mbar_arrive(&ms.flush_ready);  // round it-1 is placed
                     }
                 }
-            };
+                // end of the tile: the rank warps write the last round's chunks out, then put the
+                // carried elements in the stage (ms.cfail: the last verdict at X)
+                if (!ms.cfail) compute_sync();
+            } else {
+                // a round's ranks (bucket | rank << 8, 0xffff: no position), two per word
+                uint32_t pk_cur[2] = {0xffffffffu, 0xffffffffu}, pk_nxt[2] = {0xffffffffu, 0xffffffffu};
+                uint32_t cmeta[4] = {kNone, kNone, kNone, kNone};  // carried element: bucket | position << 10
+                T cval[4];                                          // and its value
+                for (uint32_t it = 0; it <= nrounds; ++it) {
+                    // round it-2's completed chunks (placed before the last barrier Y) leave the
+                    // stage before round it-1 is placed
+                    if (it >= 2) flush_chunks((it - 2u) & 1u);
+                    if (it < nrounds) {
+                        const uint32_t R = it * round;
+                        uint16_t* tb = tbl + (it & 1u) * k * S;
+                        uint32_t* mrow = masks + rw * 32u;
+                        auto rankp = [&](auto in_c) {
+                            constexpr bool IN = decltype(in_c)::value;
+                            const uint4 words = group_philox(pk, L, Sp.o, Q0 + (R >> 2) + rw * 32u);
+                            const uint32_t v0 = R + rw * 128u + lane;
+                            uint32_t e[4];
+#pragma unroll
+                            for (uint32_t s = 0; s < 4; ++s) {
+                                const uint32_t v = v0 + 32u * s;
+                                const bool valid = IN || (v >= delta && v - delta < r);
+                                const uint32_t b = bucket_of(group_step_word(words, s), k);
+                                uint32_t* mk = mrow + (b & 31u);
+                                if (valid) atomicOr(mk, 1u << lane);
+                                uint32_t peers = bucket_peers_hi<KB>(b, kbits);
+                                __syncwarp();
+                                uint16_t* c = tb + b * S + rw;
+                                peers &= valid ? *mk : 0u;
+                                const uint32_t pre = valid ? (uint32_t)*c : 0u;
+                                __syncwarp();
+                                if (valid && (peers & lt_mask) == 0) {
+                                    *c = (uint16_t)(pre + (uint32_t)__popc(peers));
+                                    *mk = 0u;
+                                }
+                                __syncwarp();
+                                e[s] = valid ? (b | ((pre + (uint32_t)__popc(peers & lt_mask)) << 8)) : 0xffffu;
+                            }
+                            pk_nxt[0] = e[0] | (e[1] << 16);
+                            pk_nxt[1] = e[2] | (e[3] << 16);
+                        };
+                        if (R >= delta && R + round <= rv)
+                            rankp(BoolC<true>{});
+                        else
+                            rankp(BoolC<false>{});
+                    }
+                    compute_sync();  // X
+                    if (ms.cfail) break;
+                    if (it >= 1) {
+                        // place round q = it-1, the elements carried from round q-1 first
+                        const uint32_t q = it - 1u, gq = grc + q;
+                        const T* vb = bufs + (size_t)(gq % nbuf) * g.bufstride;
+                        const uint32_t sh = shift_of(q);
+                        uint16_t* tb = tbl + (q & 1u) * k * S;
+#pragma unroll
+                        for (uint32_t s = 0; s < 4; ++s)
+                            if (cmeta[s] != kNone) stage[(size_t)(cmeta[s] & 0x3FFu) * Bs + (cmeta[s] >> 10)] = cval[s];
+#pragma unroll
+                        for (uint32_t s = 0; s < 4; ++s) {
+                            const uint32_t e = (pk_cur[s >> 1] >> (16u * (s & 1u))) & 0xffffu;
+                            cmeta[s] = kNone;
+                            if (e == 0xffffu) continue;
+                            const uint32_t b = e & 0xFFu, rk = e >> 8;
+                            const uint32_t x = tb[b * S + rw] + rk;  // offset from the current chunk's start
+                            const uint32_t bi = rw * 128u + 32u * s + lane + sh;
+                            if (x < Bs) {
+                                stage[(size_t)b * Bs + x] = vb[bi];
+                                continue;
+                            }
+                            const uint32_t qx = bs_pow2 ? x >> bs_shift : x / Bs;  // chunks past the current one
+                            const uint32_t pos = x - qx * Bs;
+                            const uint32_t rbb = rb[b], run_b = run[b];
+                            const uint32_t c0 = bs_pow2 ? rbb >> bs_shift : rbb / Bs;
+                            const uint32_t c1 = bs_pow2 ? run_b >> bs_shift : run_b / Bs;
+                            const uint32_t c = c0 + qx;
+                            if (c < c1) {  // the whole chunk lies in this round: straight to its block
+                                const uint32_t j = c / cpb, jlo = c0 / cpb;
+                                uint64_t l;
+                                if (j == jlo) {
+                                    l = jloc[b];
+                                } else {
+                                    const uint32_t xj = j - jnew[b], tk = take[b];
+                                    l = xj < tk ? alo + (uint64_t)(hbase[b] + xj) * B
+                                                : kLocPool | (pbase[b] + (uint64_t)(xj - tk) * B);
+                                }
+                                if ((l & kLocPool) && (l & ~kLocPool) + B > a.pool_cap) continue;  // reported at allocation
+                                loc_ptr(l + (uint64_t)(c % cpb) * Bs)[pos] = vb[bi];
+                            } else {
+                                cmeta[s] = b | (pos << 10);
+                                cval[s] = vb[bi];
+                            }
+                        }
+                        // the warp's column of this copy of the table is read only by the warp itself
+                        __syncwarp();
+                        for (uint32_t b = lane; b < k; b += 32u) tb[b * S + rw] = 0;
+                        compute_sync();  // Y
+                    }
+                    pk_cur[0] = pk_nxt[0];
+                    pk_cur[1] = pk_nxt[1];
+                }
+                if (!ms.cfail) {
+                    flush_chunks((nrounds - 1u) & 1u);
+                    compute_sync();
+#pragma unroll
+                    for (uint32_t s = 0; s < 4; ++s)
+                        if (cmeta[s] != kNone) stage[(size_t)(cmeta[s] & 0x3FFu) * Bs + (cmeta[s] >> 10)] = cval[s];
+                }
+            }
+        } else {
+            // ---------------------------------------------------------------- compute warps
             for (uint32_t rr = 0; rr < nrounds; ++rr) {
                 const uint32_t R = rr * round;
                 const uint32_t gr = grc + rr;
@@ -381,150 +714,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                 // (barrier B lies between), while the bookkeeping warps work
                 if (rr > 0) flush_chunks(par ^ 1u);
 
-                // bookkeeping: one lane per bucket; the (bucket, warp) counts become offsets from
-                // the start of the bucket's current chunk (below Bs: the staged chunk)
-                {
-                    const int64_t e_rd = (int64_t)R + round - delta;  // elements read through this round
-                    const uint32_t e_end = min(e_rd < (int64_t)r ? (uint32_t)e_rd : r, avail);
-                    const uint32_t F = min(H, b_pow2 ? e_end >> b_shift : a.fdB.div(e_end));
-                    for (uint32_t b0 = warp * 32u; b0 < k; b0 += kComputeThreads) {
-                        const uint32_t b = b0 + lane;
-                        const bool mine = b < k;
-                        const uint32_t cur = mine ? run[b] : 0u;
-                        const uint32_t fill = bs_pow2 ? cur & (Bs - 1u) : cur % Bs;
-                        uint32_t acc = fill;
-                        if (mine) {
-                            uint16_t* col = tbl + b * S;
-                            if constexpr (KB > 0) {
-                                // loads first, in batches of eight: the stores cannot alias them,
-                                // but the compiler cannot tell, and would wait for each load in turn
-                                constexpr uint32_t NW = cls_nwr(KC, W);
-#pragma unroll
-                                for (uint32_t j0 = 0; j0 < NW; j0 += 8) {
-                                    uint32_t cv[8];
-#pragma unroll
-                                    for (uint32_t j = 0; j < 8; ++j)
-                                        if (j0 + j < NW) cv[j] = col[j0 + j];
-#pragma unroll
-                                    for (uint32_t j = 0; j < 8; ++j)
-                                        if (j0 + j < NW) {
-                                            col[j0 + j] = (uint16_t)acc;
-                                            acc += cv[j];
-                                        }
-                                }
-                            } else {
-                                for (uint32_t j = 0; j < nwr; ++j) {
-                                    const uint32_t c = col[j];
-                                    col[j] = (uint16_t)acc;
-                                    acc += c;
-                                }
-                            }
-                        }
-                        const uint32_t t = acc - fill, nr = cur + t;
-                        const uint32_t c0 = bs_pow2 ? cur >> bs_shift : cur / Bs;
-                        const uint32_t c1 = bs_pow2 ? nr >> bs_shift : nr / Bs;
-                        const bool moves = mine && c1 > c0;  // a chunk completes: blocks receive data
-                        uint32_t jlo = 0, jhi = 0, ob = kNone, jn = 0, nb = 0;
-                        uint64_t oloc = 0;
-                        if (moves) {
-                            jlo = c0 / cpb;
-                            jhi = (c1 - 1u) / cpb;
-                            ob = oblk[b];
-                            oloc = optr[b];
-                            jn = ob == jlo ? jlo + 1u : jlo;
-                            nb = jhi + 1u - jn;
-                        }
-                        uint32_t ex = nb;
-#pragma unroll
-                        for (uint32_t d = 1; d < 32u; d <<= 1) {
-                            const uint32_t y = __shfl_up_sync(0xffffffffu, ex, d);
-                            if (lane >= d) ex += y;
-                        }
-                        const uint32_t wtotal = __shfl_sync(0xffffffffu, ex, 31);
-                        ex -= nb;
-                        // whole blocks staged: completed blocks never outrun the read elements, so
-                        // the frontier binds only past H (wrap piece) and a plain add is exact;
-                        // chunks: a block is placed at its first chunk, so claim no slot past F
-                        uint32_t hb0 = 0, lim = F;
-                        if (lane == 0 && wtotal) {
-                            if (cpb == 1) {
-                                hb0 = atomicAdd(&ms.home_next, wtotal);
-                            } else {
-                                uint32_t old = *reinterpret_cast<volatile uint32_t*>(&ms.home_next), tk = 0;
-                                for (;;) {
-                                    tk = old < F ? min(wtotal, F - old) : 0u;
-                                    if (tk == 0) break;
-                                    const uint32_t prev = atomicCAS(&ms.home_next, old, old + tk);
-                                    if (prev == old) break;
-                                    old = prev;
-                                }
-                                hb0 = old;
-                                lim = old + tk;
-                            }
-                        }
-                        hb0 = __shfl_sync(0xffffffffu, hb0, 0);
-                        lim = __shfl_sync(0xffffffffu, lim, 0);
-                        const unsigned fl_mask = __ballot_sync(0xffffffffu, moves);
-                        uint32_t fl0 = 0;
-                        if (lane == 0 && fl_mask) fl0 = atomicAdd(&ms.nflush[par], (uint32_t)__popc(fl_mask));
-                        fl0 = __shfl_sync(0xffffffffu, fl0, 0);
-                        if (mine && t) {
-                            rb[b] = cur;
-                            run[b] = nr;
-                        }
-                        if (moves) {
-                            const uint32_t hb = hb0 + ex;
-                            const uint32_t tk = lim > hb ? min(nb, lim - hb) : 0u;
-                            uint64_t pb = 0;
-                            if (nb > tk) {
-                                const uint64_t need = (uint64_t)(nb - tk) * B;
-                                const uint64_t alloc = (need + a.pool_align - 1) / a.pool_align * a.pool_align;
-                                pb = atomicAdd((unsigned long long*)a.pool_used, (unsigned long long)alloc);
-                                if (pb + need > a.pool_cap) report(a.status, RIP_EWORKSPACE, 0x6202, pb);
-                            }
-                            jnew[b] = jn;
-                            take[b] = tk;
-                            hbase[b] = hb;
-                            pbase[b] = pb;
-                            auto locf = [&](uint32_t j) -> uint64_t {
-                                if (j == ob) return oloc;
-                                const uint32_t x = j - jn;
-                                if (x < tk) return alo + (uint64_t)(hb + x) * B;
-                                return kLocPool | (pb + (uint64_t)(x - tk) * B);
-                            };
-                            const uint64_t l0 = locf(jlo);
-                            jloc[b] = l0;
-                            // the staged chunk c0 completes: its flush entry
-                            flist[par * k + fl0 + (uint32_t)__popc(fl_mask & lt_mask)] =
-                                (l0 + (uint64_t)(c0 % cpb) * Bs) | ((uint64_t)b << 48);
-                            // blocks completed this round: slot words (home) or demoted records (pool)
-                            const uint32_t jc0 = b_pow2 ? cur >> b_shift : a.fdB.div(cur);
-                            const uint32_t jc1 = b_pow2 ? nr >> b_shift : a.fdB.div(nr);
-                            for (uint32_t j = jc0; j < jc1; ++j) {
-                                if (j >= (1u << kBlkBits)) report(a.status, RIP_EINVAL, 0x6203, j);
-                                const uint64_t l = locf(j);
-                                if (!(l & kLocPool)) {
-                                    const uint32_t h = b_pow2 ? (uint32_t)((l - alo) >> b_shift)
-                                                              : a.fdB.div((uint32_t)(l - alo));
-                                    a.words[hs0 + h] = kWordOcc | (b << kBlkBits) | j;
-                                } else {
-                                    if ((l & ~kLocPool) + B > a.pool_cap) continue;  // allocation failure, reported
-                                    const uint32_t rec = atomicAdd(&a.counters[2], 1u);
-                                    if (rec < a.dem_cap)
-                                        a.dem[rec] = DemRec{tr.sp, tile, b, j, l & ~kLocPool};
-                                    else
-                                        report(a.status, RIP_EWORKSPACE, 0x6204, rec);
-                                }
-                            }
-                            if ((uint64_t)(jhi + 1u) * B > nr) {
-                                oblk[b] = jhi;
-                                optr[b] = locf(jhi);
-                            } else {
-                                oblk[b] = kNone;
-                            }
-                        }
-                    }
-                }
+                book(rr, tbl);
                 // this round's input is loaded
                 if (tid == 0) {
                     if (!mbar_wait(&ms.full[gr % nbuf], (gr / nbuf) & 1u, polls)) {
@@ -670,7 +860,7 @@ bool classify_config(uint32_t k, uint32_t B, uint32_t w, ClsCfg* out) {
     auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
     size_t off = a16(sizeof(ClsMisc));
     c.off_tbl = (uint32_t)off;
-    off = a16(off + (size_t)k * c.S * 2);
+    off = a16(off + (size_t)k * c.S * 2 * (cls_pipe(k, w) ? 2u : 1u));
     c.off_u32 = (uint32_t)off;
     off = a16(off + (size_t)k * 6 * 4);
     c.off_u64 = (uint32_t)off;
@@ -682,7 +872,7 @@ bool classify_config(uint32_t k, uint32_t B, uint32_t w, ClsCfg* out) {
     const size_t fixed = off;
     const size_t buf_bytes = a16((size_t)c.bufstride * w);
     uint32_t best_d = 0, best_nbuf = 0;
-    for (uint32_t nbuf = 3; nbuf >= 2; --nbuf) {
+    for (uint32_t nbuf = cls_pipe(k, w) ? 2u : 3u; nbuf >= 2; --nbuf) {  // pipelined: two (see the kernel)
         if (fixed + nbuf * buf_bytes >= kSmemOptin) continue;
         const size_t rem = kSmemOptin - fixed - nbuf * buf_bytes;
         uint32_t d = 0;
