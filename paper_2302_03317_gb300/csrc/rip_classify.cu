@@ -77,12 +77,12 @@ struct ClsMisc {
 // Lanes of the warp whose buckets agree with the calling lane's in the bits above the low
 // five (the low five are matched through a shared-memory mask row): one ballot per bit;
 // KB > 0 fixes the bit count at compile time.
-template <int KB>
+template <int KB, int LO = 5>
 __device__ __forceinline__ uint32_t bucket_peers_hi(uint32_t b, uint32_t kbits) {
     uint32_t peers = 0xffffffffu;
     if constexpr (KB > 0) {
 #pragma unroll
-        for (int i = 5; i < KB; ++i) {
+        for (int i = LO; i < KB; ++i) {
             const bool bit = (b >> i) & 1u;
             const uint32_t m = __ballot_sync(0xffffffffu, bit);
             peers &= bit ? m : ~m;
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
     T* pool = reinterpret_cast<T*>(a.pool);
     const uint32_t polls = a.wait_polls ? a.wait_polls : kMbarPolls;  // hand-off waits
 
-    for (uint32_t j = tid; j < nwr * 32u; j += blockDim.x) masks[j] = 0;  // kept zero after every step
+    for (uint32_t j = tid; j < nwr * (PIPE ? 64u : 32u); j += blockDim.x) masks[j] = 0;  // kept zero after every step
     if (tid == 0) {
         for (uint32_t i = 0; i < nbuf; ++i) mbar_init(&ms.full[i], 1);
         mbar_init(&ms.flush_ready, 1);
@@ -567,7 +567,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                     if (it < nrounds) {
                         const uint32_t R = it * round;
                         uint16_t* tb = tbl + (it & 1u) * k * S;
-                        uint32_t* mrow = masks + rw * 32u;
+                        uint32_t* mrow = masks + rw * 64u;  // 64 entries: the low six bucket bits
                         auto rankp = [&](auto in_c) {
                             constexpr bool IN = decltype(in_c)::value;
                             const uint4 words = group_philox(pk, L, Sp.o, Q0 + (R >> 2) + rw * 32u);
@@ -578,9 +578,9 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                                 const uint32_t v = v0 + 32u * s;
                                 const bool valid = IN || (v >= delta && v - delta < r);
                                 const uint32_t b = bucket_of(group_step_word(words, s), k);
-                                uint32_t* mk = mrow + (b & 31u);
+                                uint32_t* mk = mrow + (b & 63u);
                                 if (valid) atomicOr(mk, 1u << lane);
-                                uint32_t peers = bucket_peers_hi<KB>(b, kbits);
+                                uint32_t peers = bucket_peers_hi<KB, 6>(b, kbits);
                                 __syncwarp();
                                 uint16_t* c = tb + b * S + rw;
                                 peers &= valid ? *mk : 0u;
@@ -868,7 +868,7 @@ bool classify_config(uint32_t k, uint32_t B, uint32_t w, ClsCfg* out) {
     c.off_flist = (uint32_t)off;
     off = a16(off + (size_t)k * 2 * 8);
     c.off_mask = (uint32_t)off;
-    off = a16(off + (size_t)c.nwr * 32 * 4);
+    off = a16(off + (size_t)c.nwr * (cls_pipe(k, w) ? 64 : 32) * 4);  // mask rows
     const size_t fixed = off;
     const size_t buf_bytes = a16((size_t)c.bufstride * w);
     uint32_t best_d = 0, best_nbuf = 0;
