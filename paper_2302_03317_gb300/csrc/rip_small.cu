@@ -304,23 +304,33 @@ __device__ void finish_children(SmallShared& sh, uint16_t* P0, uint16_t* X, uint
         if (size == 1 || plan.is_leaf(size, L + 1)) {
             uint16_t* Z = Y + a + sb;
             const uint16_t* H = X + a + sb;
+            // The lanes of a warp run their chains staggered: a lane idles its first d steps, d
+            // chosen so that at every step the lanes' positions i have distinct 16-bit indices
+            // modulo 32, i.e. distinct shared-memory banks for H[i], Z[i] and out[i] (the chains
+            // start at random offsets and otherwise collide; measured as most of the solver's
+            // bank conflicts).  Each chain still takes its steps in order.
+            const uint32_t d = ((threadIdx.x & 31u) - (a + sb + size - 1u)) & 31u;
             if (Y != P0) {
                 // the swap chain writes each final position straight to P0: step i fixes
                 // position i (later steps touch only positions below i), so only Z[j] is
                 // written back; out may coincide with H, whose entry i is read before
                 uint16_t* out = P0 + a + sb;
                 uint32_t j = size > 1 ? H[size - 1] : 0u;
-                for (uint32_t i = size - 1; i >= 1; --i) {
-                    const uint32_t jn = i > 1 ? H[i - 1] : 0u;  // entry i-1 is not written at step i
-                    const uint16_t zj = Z[j];
-                    const uint16_t zi = Z[i];
-                    out[i] = zj;
-                    Z[j] = zi;
-                    j = jn;
+                if (size > 1) {
+                    for (uint32_t i = size - 1 + d; i >= 1; --i) {
+                        if (i >= size) continue;  // not started
+                        const uint32_t jn = i > 1 ? H[i - 1] : 0u;  // entry i-1 is not written at step i
+                        const uint16_t zj = Z[j];
+                        const uint16_t zi = Z[i];
+                        out[i] = zj;
+                        Z[j] = zi;
+                        j = jn;
+                    }
                 }
                 out[0] = Z[0];
-            } else {
-                for (uint32_t i = size - 1; i >= 1; --i) {
+            } else if (size > 1) {
+                for (uint32_t i = size - 1 + d; i >= 1; --i) {
+                    if (i >= size) continue;  // not started
                     const uint32_t j = H[i];
                     const uint16_t zi = Z[i];
                     Z[i] = Z[j];
