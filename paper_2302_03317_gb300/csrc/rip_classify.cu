@@ -250,6 +250,10 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                     const uint32_t b = b0 + lane;
                     const bool mine = b < k;
                     const uint32_t cur = mine ? run[b] : 0u;
+                    // the open block's index and location, loaded beside the run length (the
+                    // shared-memory round trips are the bookkeeping's latency)
+                    const uint32_t ob_ld = mine ? oblk[b] : kNone;
+                    const uint64_t oloc_ld = mine ? optr[b] : 0ull;
                     const uint32_t fill = bs_pow2 ? cur & (Bs - 1u) : cur % Bs;
                     uint32_t acc = fill;
                     if (mine) {
@@ -288,23 +292,38 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                     if (moves) {
                         jlo = c0 / cpb;
                         jhi = (c1 - 1u) / cpb;
-                        ob = oblk[b];
-                        oloc = optr[b];
+                        ob = ob_ld;
+                        oloc = oloc_ld;
                         jn = ob == jlo ? jlo + 1u : jlo;
                         nb = jhi + 1u - jn;
                     }
-                    uint32_t ex = nb;
+                    // exclusive prefix of nb over the warp's buckets: nb is almost always 0 or 1, so
+                    // ballots give it (their bits need no trip through the shared-memory unit, which
+                    // the ranking warps keep busy); a shuffle scan where some bucket opened more
+                    uint32_t ex, wtotal;
+                    if (!__any_sync(0xffffffffu, nb > 2u)) {
+                        const uint32_t m1 = __ballot_sync(0xffffffffu, nb >= 1u);
+                        const uint32_t m2 = __ballot_sync(0xffffffffu, nb >= 2u);
+                        ex = (uint32_t)__popc(m1 & lt_mask) + (uint32_t)__popc(m2 & lt_mask);
+                        wtotal = (uint32_t)__popc(m1) + (uint32_t)__popc(m2);
+                    } else {
+                        ex = nb;
 #pragma unroll
-                    for (uint32_t d = 1; d < 32u; d <<= 1) {
-                        const uint32_t y = __shfl_up_sync(0xffffffffu, ex, d);
-                        if (lane >= d) ex += y;
+                        for (uint32_t d = 1; d < 32u; d <<= 1) {
+                            const uint32_t y = __shfl_up_sync(0xffffffffu, ex, d);
+                            if (lane >= d) ex += y;
+                        }
+                        wtotal = __shfl_sync(0xffffffffu, ex, 31);
+                        ex -= nb;
                     }
-                    const uint32_t wtotal = __shfl_sync(0xffffffffu, ex, 31);
-                    ex -= nb;
                     // whole blocks staged: completed blocks never outrun the read elements, so
                     // the frontier binds only past H (wrap piece) and a plain add is exact;
                     // chunks: a block is placed at its first chunk, so claim no slot past F
-                    uint32_t hb0 = 0, lim = F;
+                    // the warp's flush-list entries and home slots: lane 0 issues both claims at
+                    // once and one round of shuffles hands the bases out
+                    const unsigned fl_mask = __ballot_sync(0xffffffffu, moves);
+                    uint32_t hb0 = 0, lim = F, fl0 = 0;
+                    if (lane == 0 && fl_mask) fl0 = atomicAdd(&ms.nflush[par], (uint32_t)__popc(fl_mask));
                     if (lane == 0 && wtotal) {
                         if (cpb == 1) {
                             hb0 = atomicAdd(&ms.home_next, wtotal);
@@ -323,9 +342,6 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                     }
                     hb0 = __shfl_sync(0xffffffffu, hb0, 0);
                     lim = __shfl_sync(0xffffffffu, lim, 0);
-                    const unsigned fl_mask = __ballot_sync(0xffffffffu, moves);
-                    uint32_t fl0 = 0;
-                    if (lane == 0 && fl_mask) fl0 = atomicAdd(&ms.nflush[par], (uint32_t)__popc(fl_mask));
                     fl0 = __shfl_sync(0xffffffffu, fl0, 0);
                     if (mine && t) {
                         rb[b] = cur;
@@ -528,7 +544,8 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
             if (bookw) {
                 for (uint32_t it = 0; it <= nrounds; ++it) {
                     if (it >= 1) book(it - 1, tbl + ((it - 1) & 1u) * k * S);
-                    // thread 0 (a bookkeeping thread): round it-1's input is loaded
+                    // thread 0 (a bookkeeping thread): round it-1's input is loaded (measured
+                    // faster here than on a rank warp, although the rank warps finish first)
                     if (tid == 0) {
                         if (it >= 1) {
                             const uint32_t gq = grc + it - 1;
@@ -571,13 +588,18 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                         auto rankp = [&](auto in_c) {
                             constexpr bool IN = decltype(in_c)::value;
                             const uint4 words = group_philox(pk, L, Sp.o, Q0 + (R >> 2) + rw * 32u);
+                            // the lane's four buckets (k <= 256: the top KB bits of each word) in one
+                            // word, so a step needs one shuffle instead of four
+                            const uint32_t pb = bucket_of(words.x, k) | (bucket_of(words.y, k) << 8) |
+                                                (bucket_of(words.z, k) << 16) | (bucket_of(words.w, k) << 24);
                             const uint32_t v0 = R + rw * 128u + lane;
                             uint32_t e[4];
 #pragma unroll
                             for (uint32_t s = 0; s < 4; ++s) {
                                 const uint32_t v = v0 + 32u * s;
                                 const bool valid = IN || (v >= delta && v - delta < r);
-                                const uint32_t b = bucket_of(group_step_word(words, s), k);
+                                const uint32_t src = __shfl_sync(0xffffffffu, pb, (int)(8u * s + (lane >> 2)));
+                                const uint32_t b = (src >> (8u * (lane & 3u))) & 0xFFu;
                                 uint32_t* mk = mrow + (b & 63u);
                                 if (valid) atomicOr(mk, 1u << lane);
                                 uint32_t peers = bucket_peers_hi<KB, 6>(b, kbits);
