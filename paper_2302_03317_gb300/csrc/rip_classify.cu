@@ -403,11 +403,14 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
 
             // the chunks that round pp's bookkeeping listed as complete go to their blocks, 16 bytes
             // (or one element) per thread, spread over many warps instead of queueing behind one
-            // copy engine; the warps that do the bookkeeping (one lane per bucket, on the round's
-            // critical path) take no share when others are left
-            const uint32_t fw0 = k < kComputeThreads ? k / 32u : 0u;  // first flushing warp
-            const uint32_t fth = kComputeThreads - fw0 * 32u;          // flushing threads
-            const uint32_t ftid = tid - fw0 * 32u;                     // (wraps for the others)
+            // copy engine. The flushing warps are those on no critical path: with fewer ranking
+            // warps than compute warps (k >= 512, 16-byte records) the warps that do not rank, while
+            // the others rank; else the warps that do not book (one lane per bucket, on the round's
+            // critical path) while the others book, or all warps when every warp books.
+            const bool flush_early = !PIPE && nwr < kIoWarp;
+            const uint32_t fw0 = flush_early ? nwr : (k < kComputeThreads ? k / 32u : 0u);  // first flushing warp
+            const uint32_t fth = kComputeThreads - fw0 * 32u;  // flushing threads
+            const uint32_t ftid = tid - fw0 * 32u;             // (wraps for the others)
             auto flush_chunks = [&](uint32_t pp) {
                 if (warp < fw0) return;
                 const uint32_t nf = ms.nflush[pp];
@@ -692,6 +695,9 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                 const uint32_t gr = grc + rr;
                 const uint32_t par = rr & 1u;
                 if (tid == 0) ms.nflush[par] = 0;
+                // the previous round's completed chunks leave the stage before this round places
+                // (barriers A and B lie between)
+                if (flush_early && rr > 0) flush_chunks(par ^ 1u);
 
                 // rank: lanes of a step with the same bucket read the warp's running count
                 // together, the lowest of them writes it back advanced by their number
@@ -734,7 +740,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                 compute_sync();  // A
                 // the previous round's completed chunks leave the stage before this round places
                 // (barrier B lies between), while the bookkeeping warps work
-                if (rr > 0) flush_chunks(par ^ 1u);
+                if (!flush_early && rr > 0) flush_chunks(par ^ 1u);
 
                 book(rr, tbl);
                 // this round's input is loaded

@@ -670,7 +670,9 @@ __device__ __forceinline__ typename Elem<W>::T* load_smem(const Sub& s, typename
     bulk_range(0u, nA, gA, fa, aLo, aHi);
     bulk_range(nA, m, gB, fb, bLo, bHi);
     if (bLo == bHi) bLo = bHi = m;
-    if (tid == 0) {
+    // issued by the first thread of the last warp, which takes no part in the write-back of the
+    // previous subproblem: a bulk copy issued after the thread's own global stores waits for them
+    if (tid == blockDim.x - 32u) {
         const uint32_t bytes = (aHi - aLo + bHi - bLo) * (uint32_t)W;
         if (bytes) {
             mbar_arrive_expect_tx(load_bar, bytes);
@@ -861,16 +863,19 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(SmallArgs args) {
         }
         __syncthreads();
         if (!wait_data()) break;
+        // the write-back leaves out the last warp, which issues the next subproblem's bulk copy
+        const uint32_t gth = blockDim.x - 32u;
         if (in_place) {
-            for (uint32_t i = tid; i < m; i += blockDim.x) base[s.o + i] = D[i];
-        } else {
+            if (tid < gth)
+                for (uint32_t i = tid; i < m; i += gth) base[s.o + i] = D[i];
+        } else if (tid < gth) {
             // four independent gathers in flight per thread
-            for (uint32_t i0 = tid; i0 < m; i0 += 4u * blockDim.x) {
+            for (uint32_t i0 = tid; i0 < m; i0 += 4u * gth) {
                 uint32_t j[4];
                 T v[4];
 #pragma unroll
                 for (uint32_t u = 0; u < 4; ++u) {
-                    const uint32_t i = i0 + u * blockDim.x;
+                    const uint32_t i = i0 + u * gth;
                     j[u] = i < m ? (uint32_t)P0[i] : 0u;
                 }
 #pragma unroll
@@ -878,7 +883,7 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(SmallArgs args) {
                     if (j[u] < m) v[u] = D[j[u]];
 #pragma unroll
                 for (uint32_t u = 0; u < 4; ++u) {
-                    const uint32_t i = i0 + u * blockDim.x;
+                    const uint32_t i = i0 + u * gth;
                     if (i >= m) break;
                     if (j[u] < m) base[s.o + i] = v[u];
                     else report(args.status, RIP_EINTERNAL, 0x5107, j[u]);  // never read outside the subproblem
