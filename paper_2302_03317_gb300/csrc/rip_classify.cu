@@ -357,10 +357,6 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                             pb = atomicAdd((unsigned long long*)a.pool_used, (unsigned long long)alloc);
                             if (pb + need > a.pool_cap) report(a.status, RIP_EWORKSPACE, 0x6202, pb);
                         }
-                        jnew[b] = jn;
-                        take[b] = tk;
-                        hbase[b] = hb;
-                        pbase[b] = pb;
                         auto locf = [&](uint32_t j) -> uint64_t {
                             if (j == ob) return oloc;
                             const uint32_t x = j - jn;
@@ -368,7 +364,16 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                             return kLocPool | (pb + (uint64_t)(x - tk) * B);
                         };
                         const uint64_t l0 = locf(jlo);
-                        jloc[b] = l0;
+                        // the placement reads these only for a chunk that lies wholly inside the
+                        // round (x >= Bs and c < c1): never unless the round crosses two chunk
+                        // boundaries of the bucket (rare), so the stores are skipped otherwise
+                        if (c1 >= c0 + 2u) {
+                            jnew[b] = jn;
+                            take[b] = tk;
+                            hbase[b] = hb;
+                            pbase[b] = pb;
+                            jloc[b] = l0;
+                        }
                         // the staged chunk c0 completes: its flush entry
                         flist[par * k + fl0 + (uint32_t)__popc(fl_mask & lt_mask)] =
                             (l0 + (uint64_t)(c0 % cpb) * Bs) | ((uint64_t)b << 48);
