@@ -115,7 +115,12 @@ __host__ __device__ constexpr uint32_t cls_nwr(uint32_t k, uint32_t w) {
                ? (k >= 1024u ? 16384u / k : 8192u / k)
                : (w >= 16 ? 16u : kIoWarp);
 }
-__host__ __device__ constexpr uint32_t cls_stride(uint32_t k, uint32_t w) { return (cls_nwr(k, w) + 1u) | 1u; }  // odd
+// Table stride per bucket (16-bit entries, more than nwr): odd, or for pipelined rounds twice an
+// odd number -- a warp's entries of 32 buckets still fall in distinct banks, and every column starts
+// on a 4-byte boundary, so the bookkeeping reads and writes it two entries at a time.
+__host__ __device__ constexpr uint32_t cls_stride(uint32_t k, uint32_t w) {
+    return cls_pipe(k, w) ? ((cls_nwr(k, w) + 1u) / 2u | 1u) * 2u : (cls_nwr(k, w) + 1u) | 1u;
+}
 
 __device__ __forceinline__ void compute_sync() {
     asm volatile("bar.sync 1, %0;" ::"r"(kComputeThreads) : "memory");
@@ -258,7 +263,25 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                     uint32_t acc = fill;
                     if (mine) {
                         uint16_t* col = tb + b * S;
-                        if constexpr (KB > 0) {
+                        if constexpr (PIPE) {
+                            // two entries per 32-bit word (the column starts 4-byte aligned), all
+                            // loads first; with an odd count the last word's upper entry is padding
+                            // that stays zero
+                            constexpr uint32_t NW = cls_nwr(KC, W), NW2 = (NW + 1u) / 2u;
+                            static_assert(cls_stride(KC, W) % 4u == 2u, "4-byte aligned columns");
+                            uint32_t* col32 = reinterpret_cast<uint32_t*>(col);
+                            uint32_t cv[NW2];
+#pragma unroll
+                            for (uint32_t j = 0; j < NW2; ++j) cv[j] = col32[j];
+#pragma unroll
+                            for (uint32_t j = 0; j < NW2; ++j) {
+                                const uint32_t lo = cv[j] & 0xFFFFu;
+                                const uint32_t hi = (2u * j + 1u < NW) ? cv[j] >> 16 : 0u;
+                                const uint32_t a1 = acc + lo;
+                                col32[j] = (acc & 0xFFFFu) | ((2u * j + 1u < NW ? a1 & 0xFFFFu : 0u) << 16);
+                                acc = a1 + hi;
+                            }
+                        } else if constexpr (KB > 0) {
                             // loads first, in batches of eight: the stores cannot alias them,
                             // but the compiler cannot tell, and would wait for each load in turn
                             constexpr uint32_t NW = cls_nwr(KC, W);
