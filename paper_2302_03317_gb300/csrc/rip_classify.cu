@@ -575,18 +575,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
             if (bookw) {
                 for (uint32_t it = 0; it <= nrounds; ++it) {
                     if (it >= 1) book(it - 1, tbl + ((it - 1) & 1u) * k * S);
-                    // thread 0 (a bookkeeping thread): round it-1's input is loaded (measured
-                    // faster here than on a rank warp, although the rank warps finish first)
-                    if (tid == 0) {
-                        if (it >= 1) {
-                            const uint32_t gq = grc + it - 1;
-                            if (!mbar_wait(&ms.full[gq % nbuf], (gq / nbuf) & 1u, polls)) {
-                                report(a.status, RIP_ETIMEOUT, 0x6207, gq);
-                                ms.fail = 1;
-                            }
-                        }
-                        ms.cfail = ms.fail;  // one verdict for all compute warps
-                    }
+                    if (tid == 0) ms.cfail = ms.fail;  // one verdict for all compute warps
                     compute_sync();  // X
                     if (ms.cfail) {
                         if (tid == 0) mbar_arrive(&ms.flush_ready);  // lets the I/O warp see the failure
@@ -595,6 +584,16 @@ __global__ void __launch_bounds__(kClassifyThreads, 1) classify_kernel(LevelArgs
                     // round it's flush list starts empty: the list of the same parity (round it-2)
                     // was written out before barrier X
                     if (tid == 0 && it < nrounds) ms.nflush[it & 1u] = 0;
+                    // round it's input, placed after the next barrier X: thread 0 waits for it now,
+                    // while the bookkeeping warps have nothing else to do (a failure reaches all
+                    // compute warps through the verdict taken before that barrier)
+                    if (tid == 0 && it < nrounds) {
+                        const uint32_t gq = grc + it;
+                        if (!mbar_wait(&ms.full[gq % nbuf], (gq / nbuf) & 1u, polls)) {
+                            report(a.status, RIP_ETIMEOUT, 0x6207, gq);
+                            ms.fail = 1;
+                        }
+                    }
                     if (it >= 1) {
                         compute_sync();  // Y
                         if (tid == 0) mbar_arrive(&ms.flush_ready);  // round it-1 is placed
