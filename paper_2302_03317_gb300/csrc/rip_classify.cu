@@ -25,7 +25,9 @@
 //            per bucket, 32 buckets per warp), blocks completed, home slots or
 //            pool blocks for blocks that receive data, slot words
 //            -- meanwhile the other warps write the chunks completed by the
-//               previous round to their blocks with 16-byte stores
+//               previous round to their blocks with 16-byte stores (with fewer
+//               ranking warps than compute warps, the warps that do not rank
+//               do so during the ranking instead)
 //   place    every element goes to its bucket's shared-memory chunk (Bs
 //            elements, Bs divides B), straight to its block in global memory
 //            when its whole chunk lies inside this round, or is carried into
@@ -39,6 +41,11 @@
 // the next round wait in registers, so a round's buffer is free as soon as it
 // is placed.  With one barrier per phase the bookkeeping (latency-bound, k
 // lanes) hides behind the ranking (throughput-bound) instead of following it.
+// Both groups then wait mostly on the shared-memory unit (loads, stores,
+// atomics and shuffles share its queue), so these rounds spend few shared-memory
+// operations: 64-entry mask rows, a lane's four buckets packed into one word
+// (one shuffle per step), and a table stride that lets the bookkeeping scan two
+// counts per 32-bit word.
 //
 // A block gets its location when its first chunk is written.  A home slot h
 // may be used once the tile's elements [0, (h+1)B) have been read; otherwise
