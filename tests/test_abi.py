@@ -138,3 +138,25 @@ def test_allocation_failure_hook_and_wait_limit_hook_exist():
     """The testing hooks of the failure paths are plain host setters (no device needed)."""
     rip.rip_debug_fail_allocations(0)
     rip.rip_debug_set_wait_limit(0)
+
+
+def test_plan_array_matches_field_by_field_conversion():
+    """The batch plan array (each distinct plan converted once, assembled in one copy) holds the same
+    bytes as converting every plan on its own: shared list objects, equal plans in distinct objects,
+    default plans and raw rip_plan structs alike."""
+    shared = rip.Plan(ks=[128, 128], Ts=[16384, 1 << 28], Bs=[256, 256], base=4096, max_levels=0)
+    plans = []
+    for i in range(300):
+        if i % 3 == 0:
+            plans.append(rip.Plan(ks=shared.ks, Ts=shared.Ts, Bs=shared.Bs, base=4096, max_levels=i % 2))
+        elif i % 3 == 1:
+            plans.append(rip.rip_default_plan(1000 + 977 * i, 4 << (i % 3)))
+        else:
+            plans.append(rip.Plan(ks=[64], Ts=[8192 + 64 * (i % 5)], Bs=[64], base=4096 + i, max_levels=0).to_c())
+    got = rip._plan_array(plans)
+    want = (rip.rip_plan * len(plans))()
+    for i, p in enumerate(plans):
+        want[i] = p.to_c() if isinstance(p, rip.Plan) else p
+    assert bytes(got) == bytes(want)
+    with pytest.raises(ValueError):
+        rip._plan_array([rip.Plan(ks=[64, 64], Ts=[8192], Bs=[64])])
